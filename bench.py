@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Throughput of the fused meshless-LBM step on one GB300 (or N replicas under torchrun).
+
+Workload (default ``tgv_large``): Taylor-Green vortex on a 2048 x 2048 lattice jittered by
++-0.3 h (seed 3), N_L = 30 nearest-neighbour stencils, cubic PHS + degree-4 polynomials,
+FP64 shape vectors, dx_ml = h, tau = 0.8, u0 = 0.01 (lattice units).  One bench step = one
+time step of the whole hot path (pull-stream, bounce-back, collide) over all 4,194,304 nodes.
+
+Reported: GNUPS of the FP32 deviation-storage step (inputs resident in HBM), the FP64 step
+beside it, the FP32-vs-FP64 relative L2 velocity error after a long run, the HBM roofline of
+the step kernel, an end-to-end figure through host buffers, sampled GPU clocks and the CPU
+oracle as a baseline.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MLBM GNUPS (node-steps/s) & % HBM peak, FP32 vs FP64 step at L2 err ≤1e-6"
+UNIT = "GNUPS"
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    # name: (n_side, K, degree, tau, u0)
+    "tgv_large": dict(n_side=2048, K=30, deg=4, tau=0.8, u0=0.01, seed=3),
+    "tgv_512": dict(n_side=512, K=30, deg=4, tau=0.8, u0=0.01, seed=3),
+    "tgv_small": dict(n_side=32, K=12, deg=2, tau=0.8, u0=0.01, seed=1),
+}
+# CPU baseline sample: the same recipe on a 128 x 128 cloud
+CPU_SAMPLE = dict(n_side=128, K=30, deg=4, tau=0.8, u0=0.01, seed=3)
+
+
+def step_bytes_per_node(K: int, dtype_bytes: int) -> int:
+    """Algorithmic bytes of one node update: 8 K shape-vector entries, K stencil indices
+    (int32), the nine populations read once and written once."""
+    return 8 * K * dtype_bytes + 4 * K + 2 * 9 * dtype_bytes
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", HBM_FALLBACK_GBS)), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def _step_source_hash():
+    h = hashlib.sha256()
+    for f in ("step.cu", "d2q9_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2306_01525_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(dtype_name):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary, if the kernel
+    source is unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", f"step_{dtype_name}_tgv_large.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != _step_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.strip()]
+        self.tmp.close()
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = max(smax, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_gnups(seconds: float, steps=None, warmup: int = 0):
+    """Time the FP64 CPU oracle's step on the bounded sample cloud (all host cores)."""
+    import mlbm_inputs as mi
+    import oracle
+
+    c = CPU_SAMPLE
+    xy = mi.jittered_lattice(c["n_side"], 0.3, seed=c["seed"])
+    dx = 1.0 / c["n_side"]
+    sidx, W = oracle.weights(xy, c["K"], c["deg"], dx, box=(1.0, 1.0))
+    st = oracle.Stepper(sidx, W, c["tau"])
+    rho, u, v = mi.tgv_initial(xy, c["u0"])
+    f = oracle.init_equilibrium(rho, u, v)
+    for _ in range(warmup):
+        f = st.step(f)
+    n = xy.shape[1]
+    done, t0 = 0, time.perf_counter()
+    while True:
+        f = st.step(f)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el >= seconds and done >= 3):
+            break
+    return dict(value=n * done / el / 1e9, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"FP64 oracle step on a {c['n_side']}x{c['n_side']} jittered cloud of the "
+                       f"same recipe (N_L={c['K']}, degree {c['deg']}), {done} steps, "
+                       f"{el:.1f} s"), done, el
+
+
+def _config(workload, world):
+    wl = WORKLOADS[workload]
+    n_side, K, deg = wl["n_side"], wl["K"], wl["deg"]
+    N = n_side * n_side
+    return {
+        "workload": f"tgv_{n_side}sq_k{K}_d{deg}",
+        "nodes": N, "stencil": K, "degree": deg, "tau": wl["tau"], "u0": wl["u0"], "dx_ml": "h",
+        "geometry": "periodic unit square, lattice jittered +-0.3h",
+        "parallelism": "replicas" if world > 1 else "single",
+        "l2_flush": "inputs larger than L2 (FP32 shape vectors %.2f GB + 2 states)" % (8 * K * 4 * N / 1e9),
+    }
+
+
+def _dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = _dist_setup()
+    if rank != 0:
+        return 0
+    # the oracle: each step one oracle time step over the bounded sample cloud
+    res, done, el = cpu_oracle_gnups(0.0, steps=args.steps, warmup=args.warmup)
+    c = CPU_SAMPLE
+    n = c["n_side"] ** 2
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args.workload, 1),
+        "cpu_baseline": res,
+        "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mlbm(args):
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    world, rank, local = _dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    wl = WORKLOADS[args.workload]
+    n_side, K, deg, tau, u0 = wl["n_side"], wl["K"], wl["deg"], wl["tau"], wl["u0"]
+    dx = 1.0 / n_side
+    t0 = time.perf_counter()
+    xy = mi.jittered_lattice(n_side, 0.3, seed=wl["seed"])
+    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx)
+    cloud = mlbm.build_cloud(xy, seg)
+    t_cloud = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w = mlbm.build_weights(cloud)
+    torch.cuda.synchronize()
+    t_weights = time.perf_counter() - t0
+    N = w.n
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, u0)
+    td = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    rho_d, u_d, v_d = td(rho), td(u), td(v)
+    del xy, cloud
+
+    def fresh(dtype):
+        tdt = torch.float32 if dtype == mlbm.F32 else torch.float64
+        a = torch.empty(9 * N, dtype=tdt, device=dev)
+        b = torch.empty_like(a)
+        mlbm.init(w, params, dtype, rho_d, u_d, v_d, a)
+        return a, b
+
+    def timed_steps(dtype, steps, warmup, clocks=None):
+        a, b = fresh(dtype)
+        a2 = mlbm.run(w, params, dtype, a, b, warmup)
+        b2 = b if a2 is a else a
+        stream = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mlbm.run(w, params, dtype, a2, b2, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop() if clocks else None
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        return ms, clk
+
+    # ---------------------------------------------------------------- FP32 (headline)
+    clocks = ClockSampler(local)
+    ms32, clk = timed_steps(mlbm.F32, args.steps, args.warmup, clocks)
+    ms_step32 = ms32 / args.steps
+    gnups32 = N * world * args.steps / (ms32 * 1e-3) / 1e9
+    # ---------------------------------------------------------------- FP64 beside it
+    s64 = max(3, min(args.steps, 100))
+    ms64, _ = timed_steps(mlbm.F64, s64, max(3, min(args.warmup, 5)))
+    ms_step64 = ms64 / s64
+    gnups64 = N * world * s64 / (ms64 * 1e-3) / 1e9
+    # ---------------------------------------------------------------- precision after a run
+    err = None
+    if args.err_steps > 0:
+        a32, b32 = fresh(mlbm.F32)
+        a64, b64 = fresh(mlbm.F64)
+        r32 = mlbm.run(w, params, mlbm.F32, a32, b32, args.err_steps)
+        r64 = mlbm.run(w, params, mlbm.F64, a64, b64, args.err_steps)
+        _, u32, v32 = mlbm.moments(w, params, mlbm.F32, r32)
+        _, u64, v64 = mlbm.moments(w, params, mlbm.F64, r64)
+        s = mlbm.norms(w, u32, u64, v32, v64)
+        err = float(np.sqrt(s[0] / s[1]))
+        del a32, b32, a64, b64, r32, r64
+    # ---------------------------------------------------------------- end to end
+    e2e_steps = max(3, min(10, args.steps))
+    st_bytes = 9 * N * 4
+    h_in = torch.empty(9 * N, dtype=torch.float32, pin_memory=True)
+    h_out = torch.empty(9 * N, dtype=torch.float32, pin_memory=True)
+    a, b = fresh(mlbm.F32)
+    h_in.copy_(a)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        a.copy_(h_in, non_blocking=True)
+        mlbm.step(w, params, mlbm.F32, a, b)
+        h_out.copy_(b, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    gnups_e2e = N * world / (ms_e2e * 1e-3) / 1e9
+    del h_in, h_out, a, b
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    peak, peak_kind = _peaks()
+    bpn32 = step_bytes_per_node(K, 4)
+    achieved = bpn32 * N / (ms_step32 * 1e-3) / 1e9
+    traffic = _ncu_traffic("f32")
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_oracle_gnups(args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": gnups32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step32, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(args.workload, world),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": peak_kind, "algorithmic_bytes_per_node": bpn32},
+        "cpu_baseline": cpu,
+        "e2e": {"value": gnups_e2e, "unit": UNIT, "h2d_bytes_per_step": st_bytes,
+                "d2h_bytes_per_step": st_bytes},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "fp64": {"value": gnups64, "unit": UNIT, "ms_per_step": ms_step64, "steps": s64,
+                 "achieved_gbs": step_bytes_per_node(K, 8) * N / (ms_step64 * 1e-3) / 1e9},
+        "speedup_fp32_vs_fp64": gnups32 / gnups64,
+        "fp32_vs_fp64_rel_l2_u": err, "error_steps": args.err_steps,
+        "setup_s": {"cloud_host": t_cloud, "weights_gpu": t_weights},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mlbm", choices=["mlbm", "reference"])
+    ap.add_argument("--workload", default="tgv_large", choices=sorted(WORKLOADS))
+    ap.add_argument("--err-steps", type=int, default=10000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mlbm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -15,7 +15,7 @@ norms the paper states:
 * ``speed_rel_error``    pointwise relative speed error, eq. (vmag_error)
 * ``residual``           relative velocity residual used as the steady-state stop, Sec. 3
 
-Parity status of each function is listed in the module ``oracle.pins`` docstring.
+Each function is checked against the paper and the mathematics in tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 
@@ -76,6 +76,8 @@ def lib():
             L.orc_shape_vector.argtypes = [i32, i32, i32, vp, vp, d, d, vp]
             L.orc_build_weights.restype = i64
             L.orc_build_weights.argtypes = [vp, vp, i64, i32, i32, d, d, d, i32, vp, vp, vp]
+            L.orc_node_weights.restype = i32
+            L.orc_node_weights.argtypes = [vp, vp, i64, i64, i32, i32, d, d, d, i32, vp, vp]
             L.orc_azimuthal_force.argtypes = [vp, vp, i64, d, vp, vp]
             L.orc_bounce_mask.argtypes = [vp, vp, i64, d, d, d, vp]
             L.orc_init_equilibrium.argtypes = [i64, vp, vp, vp, vp]
@@ -196,6 +198,18 @@ def weights(xy, K: int, deg: int, dx_ml: float, box=(0.0, 0.0), mode: str = "own
                                     1 if mode == "paper" else 0, _p(st), _p(sidx), _p(W))
     if nbad:
         raise np.linalg.LinAlgError(f"{nbad} singular collocation systems")
+    return sidx, W
+
+
+def node_weights(xy, i: int, K: int, deg: int, dx_ml: float, box=(0.0, 0.0), mode="own"):
+    """Stencil indices and shape vectors of node i alone, both [9][K], by brute force."""
+    x, y = _f64(xy[0]), _f64(xy[1])
+    sidx = np.zeros((Q, K), np.int64)
+    W = np.zeros((Q, K), np.float64)
+    nbad = lib().orc_node_weights(_p(x), _p(y), x.size, int(i), K, deg, dx_ml, box[0], box[1],
+                                  1 if mode == "paper" else 0, _p(sidx), _p(W))
+    if nbad:
+        raise np.linalg.LinAlgError(f"{nbad} singular collocation systems at node {i}")
     return sidx, W
 
 

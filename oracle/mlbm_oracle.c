@@ -348,6 +348,41 @@ int64_t orc_build_weights(const double *x, const double *y, int64_t n, int K, in
     return -nbad;
 }
 
+/* Stencils and shape vectors of ONE node i for all nine directions, found by brute force over
+ * all n nodes (own stencil of i, or in mode 1 the stencil of the node nearest to each departure
+ * point), exactly as orc_build_weights does for every node.  Outputs sidx[k*K + j] and
+ * W[k*K + j], k = 0..8.  Returns the number of singular systems. */
+int orc_node_weights(const double *x, const double *y, int64_t n, int64_t i, int K, int deg,
+                     double dx_ml, double lx, double ly, int mode, int64_t *sidx, double *W)
+{
+    int nbad = 0;
+    int64_t *st = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    double *px = (double *)malloc(sizeof(double) * (size_t)K);
+    double *py = (double *)malloc(sizeof(double) * (size_t)K);
+    for (int k = 0; k < ORC_Q; ++k) {
+        double Dx = x[i] - orc_ex[k] * dx_ml;
+        double Dy = y[i] - orc_ey[k] * dx_ml;
+        int64_t L = i;
+        if (mode == 1) orc_knn(x, y, n, Dx, Dy, 1, lx, ly, &L);
+        orc_knn(x, y, n, x[L], y[L], K, lx, ly, st);
+        for (int j = 0; j < K; ++j) {
+            px[j] = orc_wrap(x[st[j]] - x[L], lx);
+            py[j] = orc_wrap(y[st[j]] - y[L], ly);
+        }
+        double qx = orc_wrap(Dx - x[L], lx);
+        double qy = orc_wrap(Dy - y[L], ly);
+        if (orc_shape_vector(2, K, deg, px, py, qx, qy, W + (int64_t)k * K) != 0) {
+            nbad += 1;
+            for (int j = 0; j < K; ++j) W[(int64_t)k * K + j] = 0.0;
+        }
+        for (int j = 0; j < K; ++j) sidx[(int64_t)k * K + j] = st[j];
+    }
+    free(st);
+    free(px);
+    free(py);
+    return nbad;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* Annular channel (Sec. 3): body force and wall bounce-back                            */
 /* ------------------------------------------------------------------------------------ */

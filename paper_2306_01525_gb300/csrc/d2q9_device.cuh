@@ -1,0 +1,66 @@
+// D2Q9 model pieces used inside the fused kernels (Sec. 2.1 velocity set and weights,
+// eq. feq equilibrium, eq. LBM_collision BGK relaxation, Sec. 3 forcing term).
+//
+// Populations are handled in "storage form" s_k = f_k - omega_k * rho_ref: rho_ref = rho0 for
+// the FP32 deviation storage and 0 for FP64 (then s_k = f_k).  Because sum_k omega_k e_k = 0,
+// the momentum sum_k s_k e_k equals sum_k f_k e_k in both forms.
+#pragma once
+
+#include <cstdint>
+
+namespace mlbm {
+
+__host__ __device__ constexpr int ex_of(int k) {
+    return (k == 1 || k == 5 || k == 8) ? 1 : ((k == 3 || k == 6 || k == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey_of(int k) {
+    return (k == 2 || k == 5 || k == 6) ? 1 : ((k == 4 || k == 7 || k == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp_of(int k) {
+    return k == 0 ? 0 : (k <= 4 ? ((k + 1) % 4) + 1 : ((k - 5 + 2) % 4) + 5);
+}
+template <typename T>
+__host__ __device__ constexpr T omega_of(int k) {
+    return k == 0 ? T(4) / T(9) : (k <= 4 ? T(1) / T(9) : T(1) / T(36));
+}
+
+static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp");
+static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp");
+static_assert(ex_of(opp_of(6)) == -ex_of(6) && ey_of(opp_of(6)) == -ey_of(6), "opp");
+
+// Macroscopic fields of storage-form populations: drho = rho - rho_ref, and rho, u.
+template <typename T>
+__device__ __forceinline__ void moments_of(const T (&s)[9], T rho_ref, T &drho, T &rho, T &ux, T &uy) {
+    drho = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])) + s[8];
+    T mx = (s[1] - s[3]) + (s[5] - s[6]) + (s[8] - s[7]);
+    T my = (s[2] - s[4]) + (s[5] + s[6]) - (s[7] + s[8]);
+    rho = rho_ref + drho;
+    T ir = T(1) / rho;
+    ux = mx * ir;
+    uy = my * ir;
+}
+
+// Equilibrium in storage form: f^eq_k - omega_k rho_ref = omega_k (drho + rho (3 cu + 4.5 cu^2 - 1.5 u^2)).
+template <typename T>
+__device__ __forceinline__ T geq_of(int k, T drho, T rho, T ux, T uy, T usq15) {
+    T cu = T(ex_of(k)) * ux + T(ey_of(k)) * uy;
+    return omega_of<T>(k) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - usq15));
+}
+
+// In place: s <- s - (s - s^eq) / tau + omega_k e_k.g / c_s^2.  Returns the pre-collision
+// moments through rho, ux, uy.
+template <typename T>
+__device__ __forceinline__ void collide(T (&s)[9], T rho_ref, T inv_tau, T gx, T gy, T &rho, T &ux,
+                                        T &uy) {
+    T drho;
+    moments_of(s, rho_ref, drho, rho, ux, uy);
+    const T usq15 = T(1.5) * (ux * ux + uy * uy);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        T geq = geq_of<T>(k, drho, rho, ux, uy, usq15);
+        T force = omega_of<T>(k) * T(3) * (T(ex_of(k)) * gx + T(ey_of(k)) * gy);
+        s[k] = s[k] - (s[k] - geq) * inv_tau + force;
+    }
+}
+
+}  // namespace mlbm

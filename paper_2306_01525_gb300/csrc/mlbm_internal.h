@@ -1,0 +1,114 @@
+// Internal structures of the GB300 meshless LBM library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mlbm.h"
+
+namespace mlbm {
+
+constexpr int kQ = 9;
+constexpr int kMaxDegree = 8;
+constexpr int kMaxK = 128;
+
+// Monomials of total degree <= d in two variables.
+inline int num_monomials(int d) { return d < 0 ? 0 : (d + 1) * (d + 2) / 2; }
+
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+// One segment (independent simulation) as laid out in device arrays.
+struct SegmentHost {
+    mlbm_segment_desc d;
+    int64_t orig_off = 0;  // first original index of the segment
+    int64_t off = 0;       // first stored position (global)
+    int64_t n = 0;         // nodes in the segment
+    int K = 0;             // stencil size
+    int m = 0;             // monomials
+    int64_t idx_off = 0;   // offset of the [K][n] stencil block (int32 entries)
+    int64_t w_off = 0;     // offset of the [8][K][n] shape-vector block
+    int64_t csr_off = 0;   // offset of the segment's transposed-stencil entries
+};
+
+struct mlbm_cloud_impl {
+    int nseg = 0;
+    int64_t N = 0;
+    std::vector<SegmentHost> seg;
+    std::vector<double> x, y;           // stored order
+    std::vector<int64_t> perm;          // stored position -> original index
+    std::vector<int32_t> idx;           // per segment [K][n], global stored positions
+    std::vector<uint16_t> mask;         // stored order
+    std::vector<double> fdir;           // [2][N] force direction, stored order
+    std::vector<int32_t> csr_ptr;       // [N+1] transposed stencil row pointers (global)
+    std::vector<int32_t> csr_ent;       // entries e = j * n_seg + i_local (segment-local)
+    std::vector<int32_t> node_seg;      // stored position -> segment
+    int64_t idx_total = 0, w_total = 0;
+};
+
+// Device-side segment descriptor (plain old data, copied to the device).
+struct SegDev {
+    int64_t off, n, idx_off, w_off;
+    int K, m, deg, geometry;
+    double lx, ly, dx_ml, pad;
+};
+
+// A tile: a contiguous run of stored nodes of one segment processed by one CTA pass.
+struct TileDev {
+    int64_t begin;  // first stored position
+    int32_t count;  // nodes in tile
+    int32_t seg;    // segment index
+};
+
+struct GraphKey {
+    const void *a, *b;
+    int dtype;
+    int64_t chunk;
+    std::vector<double> params;
+    bool operator<(const GraphKey &o) const {
+        return std::tie(a, b, dtype, chunk, params) < std::tie(o.a, o.b, o.dtype, o.chunk, o.params);
+    }
+};
+
+struct mlbm_weights_impl {
+    int nseg = 0;
+    int64_t N = 0;
+    std::vector<SegmentHost> seg;
+    std::vector<int64_t> perm;  // host copy
+    // device arrays
+    SegDev *d_seg = nullptr;
+    TileDev *d_tiles = nullptr;
+    int ntiles = 0;
+    int tile_nodes = 0;
+    int32_t *d_idx = nullptr;
+    float *d_w32 = nullptr;
+    double *d_w64 = nullptr;
+    uint16_t *d_mask = nullptr;
+    float *d_fdir32 = nullptr;
+    double *d_fdir64 = nullptr;
+    int64_t *d_perm = nullptr;  // stored -> original
+    int32_t *d_node_seg = nullptr;
+    int32_t *d_csr_ptr = nullptr;
+    int32_t *d_csr_ent = nullptr;
+    int64_t idx_total = 0, w_total = 0;
+    bool has_mask = false;
+    // scratch (lazily allocated)
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *d_partials = nullptr;
+    int partial_slots = 0;
+    double *d_params = nullptr;  // [nseg][4] device copy of step parameters
+    std::vector<double> params_cache;
+    int num_sms = 0;
+    int step_grid[2] = {0, 0};  // persistent grid of the step kernel, [FP32, FP64]
+    int device = 0;
+    std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
+};
+
+}  // namespace mlbm
+
+struct mlbm_cloud : mlbm::mlbm_cloud_impl {};
+struct mlbm_weights : mlbm::mlbm_weights_impl {};

@@ -1,0 +1,407 @@
+// Fused meshless-LBM time step and its companions (appendix algorithm COLLIDE/STREAM reordered
+// as a pull; Sec. 2.3 semi-Lagrangian streaming; Sec. 3 forcing and wall bounce-back),
+// initial state, moments, norms and the CUDA-graph step loop.
+//
+// Step kernel: persistent CTAs walk a tile table (tiles = runs of <= 256 stored nodes of one
+// segment, largest stencils first), one thread per node.  For node i the stencil index idx[j][i]
+// is loaded once and reused by all eight moving directions; shape vectors are [dir][j][node] SoA
+// so every warp load of a weight is one fully used 128-byte line; the gathered f^post values
+// hit L1/L2 because the nodes are Morton ordered.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "d2q9_device.cuh"
+#include "mlbm_internal.h"
+
+namespace mlbm {
+
+int cuda_check_step(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MLBM_OK;
+    return fail(MLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+template <typename T>
+struct StepArgs {
+    const SegDev *__restrict__ seg;
+    const TileDev *__restrict__ tiles;
+    const int32_t *__restrict__ idx;
+    const T *__restrict__ w;
+    const uint16_t *__restrict__ mask;  // NULL when no segment has wall populations
+    const T *__restrict__ fdir;         // [2][N]
+    const double *__restrict__ params;  // [nseg][4]: tau, g, rho0, unused
+    const T *__restrict__ fin;
+    T *__restrict__ fout;
+    T *__restrict__ mom;  // optional [3][N]
+    int64_t N;
+    int ntiles;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs<T> a) {
+    constexpr bool kDev = std::is_same<T, float>::value;
+    const int64_t N = a.N;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDev tile = a.tiles[t];
+        if ((int)threadIdx.x >= tile.count) continue;
+        const int64_t p = tile.begin + threadIdx.x;
+        const SegDev &sd = a.seg[tile.seg];
+        const int64_t n = sd.n;
+        const int K = sd.K;
+        const int64_t il = p - sd.off;
+        const int32_t *__restrict__ ip = a.idx + sd.idx_off + il;
+        const T *__restrict__ wp = a.w + sd.w_off + il;
+        const int64_t KN = (int64_t)K * n;
+        T f[9];
+        f[0] = a.fin[p];
+#pragma unroll
+        for (int k = 1; k < 9; ++k) f[k] = T(0);
+        // pull-stream: fhat_k(i) = sum_j W_k[j](i) f^post_k(s_j(i))
+#pragma unroll 2
+        for (int j = 0; j < K; ++j) {
+            const int32_t nb = __ldg(ip + (int64_t)j * n);
+            const T *__restrict__ wj = wp + (int64_t)j * n;
+#pragma unroll
+            for (int k = 1; k < 9; ++k) f[k] = fma(__ldg(wj + (int64_t)(k - 1) * KN), __ldg(a.fin + (int64_t)k * N + nb), f[k]);
+        }
+        // wall bounce-back: unknown populations take the streamed opposite population
+        if (a.mask) {
+            const uint16_t mb = a.mask[p];
+            if (mb) {
+                T g[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) g[k] = f[k];
+#pragma unroll
+                for (int k = 1; k < 9; ++k)
+                    if (mb >> k & 1u) f[k] = g[opp_of(k)];
+            }
+        }
+        const double *pr = a.params + 4 * tile.seg;
+        const T inv_tau = T(1.0 / pr[0]);
+        const T gm = T(pr[1]);
+        const T rho_ref = kDev ? T(pr[2]) : T(0);
+        T gx = T(0), gy = T(0);
+        if (gm != T(0)) {
+            gx = gm * a.fdir[p];
+            gy = gm * a.fdir[N + p];
+        }
+        T rho, ux, uy;
+        collide<T>(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
+        if (a.mom) {
+            a.mom[p] = rho;
+            a.mom[N + p] = ux;
+            a.mom[2 * N + p] = uy;
+        }
+    }
+}
+
+// Initial state: equilibrium at (rho, u) plus the forcing term (its post-collision value).
+template <typename T>
+__global__ void init_kernel(const TileDev *__restrict__ tiles, int ntiles, const int64_t *__restrict__ perm,
+                            const double *__restrict__ fdir, const double *__restrict__ params,
+                            const double *__restrict__ rho_in, const double *__restrict__ ux_in,
+                            const double *__restrict__ uy_in, T *__restrict__ f, int64_t N) {
+    constexpr bool kDev = std::is_same<T, float>::value;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDev tile = tiles[t];
+        if ((int)threadIdx.x >= tile.count) continue;
+        const int64_t p = tile.begin + threadIdx.x;
+        const int64_t o = perm[p];
+        const double *pr = params + 4 * tile.seg;
+        const double rho_ref = kDev ? pr[2] : 0.0;
+        const double rho = rho_in[o], ux = ux_in[o], uy = uy_in[o];
+        const double gx = pr[1] * fdir[p], gy = pr[1] * fdir[N + p];
+        const double usq15 = 1.5 * (ux * ux + uy * uy);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double s = geq_of<double>(k, rho - rho_ref, rho, ux, uy, usq15) +
+                       omega_of<double>(k) * 3.0 * (ex_of(k) * gx + ey_of(k) * gy);
+            f[(int64_t)k * N + p] = (T)s;
+        }
+    }
+}
+
+// Macroscopic fields of the level whose post-collision state is f (collision keeps rho and
+// adds g to rho u), FP64, scattered to original order.
+template <typename T>
+__global__ void moments_kernel(const TileDev *__restrict__ tiles, int ntiles, const int64_t *__restrict__ perm,
+                               const double *__restrict__ fdir, const double *__restrict__ params,
+                               const T *__restrict__ f, double *__restrict__ rho_out,
+                               double *__restrict__ ux_out, double *__restrict__ uy_out, int64_t N) {
+    constexpr bool kDev = std::is_same<T, float>::value;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDev tile = tiles[t];
+        if ((int)threadIdx.x >= tile.count) continue;
+        const int64_t p = tile.begin + threadIdx.x;
+        const double *pr = params + 4 * tile.seg;
+        double s[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s[k] = (double)f[(int64_t)k * N + p];
+        double drho, rho, ux, uy;
+        moments_of<double>(s, kDev ? pr[2] : 0.0, drho, rho, ux, uy);
+        // remove the body force the collision added
+        ux -= pr[1] * fdir[p] / rho;
+        uy -= pr[1] * fdir[N + p] / rho;
+        const int64_t o = perm[p];
+        rho_out[o] = rho;
+        ux_out[o] = ux;
+        uy_out[o] = uy;
+    }
+}
+
+constexpr int kNormBlocks = 1024;
+constexpr int kNormThreads = 256;
+
+template <int NT>
+__device__ __forceinline__ void block_sum3(double v[3], double *sh) {
+    for (int c = 0; c < 3; ++c) {
+        sh[threadIdx.x] = v[c];
+        __syncthreads();
+        for (int s = NT / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        v[c] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kNormThreads) norms_pass1(const double *__restrict__ a, const double *__restrict__ b,
+                                                             const double *__restrict__ c, const double *__restrict__ d,
+                                                             int64_t n, double *__restrict__ partial) {
+    __shared__ double sh[kNormThreads];
+    double v[3] = {0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double e = a[i] - b[i];
+        v[0] += e * e;
+        v[1] += b[i] * b[i];
+        v[2] += a[i] * a[i];
+        if (c) {
+            double e2 = c[i] - d[i];
+            v[0] += e2 * e2;
+            v[1] += d[i] * d[i];
+            v[2] += c[i] * c[i];
+        }
+    }
+    block_sum3<kNormThreads>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) partial[3 * blockIdx.x + k] = v[k];
+}
+
+__global__ void __launch_bounds__(kNormThreads) norms_pass2(const double *__restrict__ partial, int nparts,
+                                                             double *__restrict__ out) {
+    __shared__ double sh[kNormThreads];
+    double v[3] = {0, 0, 0};
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+        for (int k = 0; k < 3; ++k) v[k] += partial[3 * i + k];
+    block_sum3<kNormThreads>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) out[k] = v[k];
+}
+
+int grid_for(const mlbm_weights *w, const void *fn, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    per_sm = std::max(1, per_sm);
+    return std::max(1, std::min(w->ntiles, per_sm * w->num_sms));
+}
+
+}  // namespace
+
+// Stream-ordered refresh of the device copy of the step parameters.
+int set_params(mlbm_weights *w, const mlbm_params *params, cudaStream_t st) {
+    if (!params) return fail(MLBM_EINVAL, "params is NULL");
+    std::vector<double> v(4 * w->nseg);
+    for (int s = 0; s < w->nseg; ++s) {
+        if (!(params[s].tau > 0.5)) return fail(MLBM_EINVAL, "tau must be > 0.5 (positive viscosity)");
+        if (!std::isfinite(params[s].g) || !std::isfinite(params[s].rho0))
+            return fail(MLBM_EINVAL, "non-finite parameter");
+        v[4 * s] = params[s].tau;
+        v[4 * s + 1] = params[s].g;
+        v[4 * s + 2] = params[s].rho0;
+        v[4 * s + 3] = 0.0;
+    }
+    if (v == w->params_cache) return MLBM_OK;
+    int rc = cuda_check_step(cudaMemcpyAsync(w->d_params, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+                             "parameter upload");
+    if (rc) return rc;
+    // the pageable source may be read after return: wait for the copy before v dies
+    rc = cuda_check_step(cudaStreamSynchronize(st), "parameter upload");
+    if (rc) return rc;
+    w->params_cache = v;
+    return MLBM_OK;
+}
+
+int check_dtype(const mlbm_weights *w, int dtype) {
+    if (dtype == MLBM_F32) return w->d_w32 ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
+    if (dtype == MLBM_F64) return w->d_w64 ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W64");
+    return fail(MLBM_EINVAL, "dtype must be MLBM_F32 or MLBM_F64");
+}
+
+template <typename T>
+int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom, cudaStream_t st) {
+    StepArgs<T> a;
+    a.seg = w->d_seg;
+    a.tiles = w->d_tiles;
+    a.idx = w->d_idx;
+    a.w = std::is_same<T, float>::value ? (const T *)w->d_w32 : (const T *)w->d_w64;
+    a.mask = w->has_mask ? w->d_mask : nullptr;
+    a.fdir = std::is_same<T, float>::value ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
+    a.params = w->d_params;
+    a.fin = (const T *)fin;
+    a.fout = (T *)fout;
+    a.mom = (T *)mom;
+    a.N = w->N;
+    a.ntiles = w->ntiles;
+    const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
+    step_kernel<T><<<grid, 256, 0, st>>>(a);
+    return cuda_check_step(cudaGetLastError(), "step_kernel launch");
+}
+
+// Persistent grids of the step kernels: CTAs resident per SM x SMs, capped by the tile count.
+void prepare_step_grids(mlbm_weights *w) {
+    w->step_grid[0] = grid_for(w, (const void *)step_kernel<float>, 256, 0);
+    w->step_grid[1] = grid_for(w, (const void *)step_kernel<double>, 256, 0);
+}
+
+int launch_step(const mlbm_weights *w, int dtype, const void *fin, void *fout, void *mom, cudaStream_t st) {
+    return dtype == MLBM_F32 ? launch_step_t<float>(w, fin, fout, mom, st)
+                             : launch_step_t<double>(w, fin, fout, mom, st);
+}
+
+}  // namespace mlbm
+
+using namespace mlbm;
+
+extern "C" {
+
+int mlbm_init(const mlbm_weights *w, const mlbm_params *params, int dtype, const double *rho,
+              const double *ux, const double *uy, void *f_out, void *stream) {
+    set_error("");
+    if (!w || !rho || !ux || !uy || !f_out) return fail(MLBM_EINVAL, "NULL argument");
+    if (dtype != MLBM_F32 && dtype != MLBM_F64) return fail(MLBM_EINVAL, "bad dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    mlbm_weights *wm = const_cast<mlbm_weights *>(w);
+    int rc = set_params(wm, params, st);
+    if (rc) return rc;
+    if (dtype == MLBM_F32) {
+        int grid = grid_for(w, (const void *)init_kernel<float>, 256, 0);
+        init_kernel<float><<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params, rho, ux,
+                                                 uy, (float *)f_out, w->N);
+    } else {
+        int grid = grid_for(w, (const void *)init_kernel<double>, 256, 0);
+        init_kernel<double><<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params, rho, ux,
+                                                  uy, (double *)f_out, w->N);
+    }
+    return cuda_check_step(cudaGetLastError(), "init_kernel launch");
+}
+
+int mlbm_step(const mlbm_weights *w, const mlbm_params *params, int dtype, const void *f_in,
+              void *f_out, void *moments, void *stream) {
+    set_error("");
+    if (!w || !f_in || !f_out) return fail(MLBM_EINVAL, "NULL argument");
+    if (f_in == f_out) return fail(MLBM_EINVAL, "f_in and f_out must not alias");
+    int rc = check_dtype(w, dtype);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = set_params(const_cast<mlbm_weights *>(w), params, st))) return rc;
+    return launch_step(w, dtype, f_in, f_out, moments, st);
+}
+
+int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
+             int64_t nsteps, void *stream) {
+    set_error("");
+    if (!w || !f_a || !f_b) return fail(MLBM_EINVAL, "NULL argument");
+    if (f_a == f_b) return fail(MLBM_EINVAL, "f_a and f_b must differ");
+    if (nsteps < 0) return fail(MLBM_EINVAL, "nsteps < 0");
+    int rc = check_dtype(w, dtype);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = set_params(w, params, st))) return rc;
+    const int64_t G = 64;  // steps per captured graph (even: the graph maps f_a back to f_a)
+    int64_t reps = nsteps / G, rem = nsteps % G;
+    if (reps > 0) {
+        GraphKey key{f_a, f_b, dtype, G, {}};
+        cudaGraphExec_t exec = nullptr;
+        auto it = w->graphs.find(key);
+        if (it != w->graphs.end()) {
+            exec = (cudaGraphExec_t)it->second;
+        } else {
+            cudaStream_t cs;
+            if ((rc = cuda_check_step(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream")))
+                return rc;
+            rc = cuda_check_step(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (int64_t i = 0; i < G && !rc; ++i)
+                rc = launch_step(w, dtype, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, cs);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cs, &graph);
+            if (!rc) rc = cuda_check_step(e, "end capture");
+            if (!rc) rc = cuda_check_step(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+            if (graph) cudaGraphDestroy(graph);
+            cudaStreamDestroy(cs);
+            if (rc) return rc;
+            w->graphs[key] = (void *)exec;
+        }
+        for (int64_t r = 0; r < reps; ++r)
+            if ((rc = cuda_check_step(cudaGraphLaunch(exec, st), "graph launch"))) return rc;
+    }
+    for (int64_t i = 0; i < rem; ++i)
+        if ((rc = launch_step(w, dtype, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, st))) return rc;
+    return MLBM_OK;
+}
+
+int mlbm_moments(const mlbm_weights *w, const mlbm_params *params, int dtype, const void *f,
+                 double *rho, double *ux, double *uy, void *stream) {
+    set_error("");
+    if (!w || !f || !rho || !ux || !uy) return fail(MLBM_EINVAL, "NULL argument");
+    if (dtype != MLBM_F32 && dtype != MLBM_F64) return fail(MLBM_EINVAL, "bad dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = set_params(const_cast<mlbm_weights *>(w), params, st);
+    if (rc) return rc;
+    if (dtype == MLBM_F32) {
+        int grid = grid_for(w, (const void *)moments_kernel<float>, 256, 0);
+        moments_kernel<float><<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params,
+                                                    (const float *)f, rho, ux, uy, w->N);
+    } else {
+        int grid = grid_for(w, (const void *)moments_kernel<double>, 256, 0);
+        moments_kernel<double><<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params,
+                                                     (const double *)f, rho, ux, uy, w->N);
+    }
+    return cuda_check_step(cudaGetLastError(), "moments_kernel launch");
+}
+
+int mlbm_norms(const mlbm_weights *w, const double *a, const double *b, const double *c,
+               const double *d, int64_t n, double *out, void *stream) {
+    set_error("");
+    if (!w || !a || !b || !out || n < 0) return fail(MLBM_EINVAL, "bad argument");
+    if ((c == nullptr) != (d == nullptr)) return fail(MLBM_EINVAL, "c and d must both be given or both NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    mlbm_weights *wm = const_cast<mlbm_weights *>(w);
+    if (!wm->d_partials) {
+        cudaError_t e = cudaMalloc((void **)&wm->d_partials, sizeof(double) * (3 * kNormBlocks + 3));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            wm->d_partials = nullptr;
+            return fail(MLBM_ENOMEM, "scratch allocation failed");
+        }
+    }
+    norms_pass1<<<kNormBlocks, kNormThreads, 0, st>>>(a, b, c, d, n, wm->d_partials);
+    norms_pass2<<<1, kNormThreads, 0, st>>>(wm->d_partials, kNormBlocks, wm->d_partials + 3 * kNormBlocks);
+    int rc = cuda_check_step(cudaGetLastError(), "norms launch");
+    if (rc) return rc;
+    rc = cuda_check_step(cudaMemcpyAsync(out, wm->d_partials + 3 * kNormBlocks, 3 * sizeof(double),
+                                         cudaMemcpyDeviceToHost, st),
+                         "norms copy");
+    if (rc) return rc;
+    return cuda_check_step(cudaStreamSynchronize(st), "norms");
+}
+
+}  // extern "C"

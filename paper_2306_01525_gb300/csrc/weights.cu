@@ -1,0 +1,481 @@
+// Batched FP64 RBF-FD shape-vector solver (Sec. 2.2 eq. shape_vector, Sec. 2.3 basis r^3 + P_d,
+// LU with partial pivoting) and construction of the device weights object.
+//
+// One warp owns one collocation system Phi_L (n = N_L + m) plus its eight right-hand sides
+// (one per moving direction) as an n x (n + 8) augmented matrix in shared memory.  Lanes run
+// over columns in the elimination (conflict-free row-major access) and over rows in the
+// pivot search.  Systems of different sizes (batched segments) share one launch: each warp
+// reads its own n from the segment table; the per-warp shared-memory slot is sized for the
+// largest system of the launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mlbm_internal.h"
+
+namespace mlbm {
+
+__constant__ signed char c_mono_px[64];  // exponent of x of monomial l
+__constant__ signed char c_mono_py[64];  // exponent of y of monomial l
+
+namespace {
+
+// D2Q9 directions of Sec. 2.1
+__constant__ int kEx[kQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kEy[kQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+__device__ __forceinline__ double d_wrap(double d, double L) {
+    if (L > 0.0) d -= L * round(d / L);
+    return d;
+}
+
+__device__ __forceinline__ double d_ipow(double v, int p) {
+    double r = 1.0;
+    for (int i = 0; i < p; ++i) r *= v;
+    return r;
+}
+
+__device__ __forceinline__ double d_mono(int l, double x, double y) {
+    return d_ipow(x, c_mono_px[l]) * d_ipow(y, c_mono_py[l]);
+}
+
+__device__ __forceinline__ double d_phi(double dx, double dy) {
+    double r = sqrt(dx * dx + dy * dy);
+    return r * r * r;
+}
+
+struct SolveArgs {
+    const SegDev *seg;
+    const double *x, *y;
+    const int32_t *idx;
+    const int32_t *node_seg;
+    double *w64;
+    float *w32;
+    unsigned long long *nbad;
+    int64_t N;
+    int slot;  // doubles per warp slot
+};
+
+__device__ __forceinline__ int ld_of(int n) { return (n + 8) | 1; }
+
+__global__ void solve_kernel(SolveArgs a) {
+    extern __shared__ double sm[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    double *A = sm + (size_t)warp * a.slot;
+    for (int64_t node = (int64_t)blockIdx.x * wpb + warp; node < a.N;
+         node += (int64_t)gridDim.x * wpb) {
+        const SegDev sd = a.seg[a.node_seg[node]];
+        const int K = sd.K, m = sd.m, n = K + m, ld = ld_of(n), nc = n + 8;
+        double *tx = A + n * ld;
+        double *ty = tx + K;
+        const int64_t il = node - sd.off;
+        const double xi = a.x[node], yi = a.y[node];
+        const double lx = sd.geometry == MLBM_GEOM_PERIODIC ? sd.lx : 0.0;
+        const double ly = sd.geometry == MLBM_GEOM_PERIODIC ? sd.ly : 0.0;
+        // stencil coordinates relative to the node (minimum image), radius
+        double rmax = 0.0;
+        for (int j = lane; j < K; j += 32) {
+            int32_t nb = a.idx[sd.idx_off + (int64_t)j * sd.n + il];
+            double dx = d_wrap(a.x[nb] - xi, lx), dy = d_wrap(a.y[nb] - yi, ly);
+            tx[j] = dx;
+            ty[j] = dy;
+            rmax = fmax(rmax, sqrt(dx * dx + dy * dy));
+        }
+        for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        const double s = rmax > 0.0 ? rmax : 1.0;
+        for (int j = lane; j < K; j += 32) {
+            tx[j] /= s;
+            ty[j] /= s;
+        }
+        __syncwarp();
+        // augmented matrix [Phi_L | phi_L(q_1) ... phi_L(q_8)], q_k = -e_k dx_ml / s
+        const double dq = sd.dx_ml / s;
+        double amax = 0.0;
+        for (int e = lane; e < n * nc; e += 32) {
+            int r = e / nc, c = e - r * nc;
+            double v;
+            if (c >= n) {
+                int k = c - n + 1;
+                double qx = -kEx[k] * dq, qy = -kEy[k] * dq;
+                v = (r < K) ? d_phi(qx - tx[r], qy - ty[r]) : d_mono(r - K, qx, qy);
+            } else if (r < K && c < K) {
+                v = d_phi(tx[r] - tx[c], ty[r] - ty[c]);
+            } else if (r < K) {
+                v = d_mono(c - K, tx[r], ty[r]);
+            } else if (c < K) {
+                v = d_mono(r - K, tx[c], ty[c]);
+            } else {
+                v = 0.0;
+            }
+            if (c < n) amax = fmax(amax, fabs(v));
+            A[r * ld + c] = v;
+        }
+        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        __syncwarp();
+        bool bad = false;
+        // LU with partial pivoting, eliminating the right-hand sides along
+        for (int p = 0; p < n; ++p) {
+            double best = -1.0;
+            int piv = p;
+            for (int r = p + lane; r < n; r += 32) {
+                double v = fabs(A[r * ld + p]);
+                if (v > best) {
+                    best = v;
+                    piv = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                int op = __shfl_xor_sync(0xffffffffu, piv, o);
+                if (ob > best || (ob == best && op < piv)) {
+                    best = ob;
+                    piv = op;
+                }
+            }
+            if (!(best > 1e-14 * amax)) {
+                bad = true;
+                break;
+            }
+            if (piv != p) {
+                for (int c = p + lane; c < nc; c += 32) {
+                    double t = A[p * ld + c];
+                    A[p * ld + c] = A[piv * ld + c];
+                    A[piv * ld + c] = t;
+                }
+            }
+            __syncwarp();
+            const double inv = 1.0 / A[p * ld + p];
+            for (int r = p + 1 + lane; r < n; r += 32) A[r * ld + p] *= inv;
+            __syncwarp();
+            for (int c = p + 1 + lane; c < nc; c += 32) {
+                const double apc = A[p * ld + c];
+                for (int r = p + 1; r < n; ++r) A[r * ld + c] = fma(-A[r * ld + p], apc, A[r * ld + c]);
+            }
+            __syncwarp();
+        }
+        if (!bad) {
+            // back substitution of the eight right-hand sides
+            for (int p = n - 1; p >= 0; --p) {
+                if (lane < 8) A[p * ld + n + lane] /= A[p * ld + p];
+                __syncwarp();
+                for (int t = lane; t < p * 8; t += 32) {
+                    int r = t >> 3, q = t & 7;
+                    A[r * ld + n + q] = fma(-A[r * ld + p], A[p * ld + n + q], A[r * ld + n + q]);
+                }
+                __syncwarp();
+            }
+            // polynomial reproduction check: sum_j w_j p_l(x_j) = p_l(q_k)
+            double err = 0.0;
+            for (int t = lane; t < 8 * m; t += 32) {
+                int q = t / m, l = t - q * m;
+                int k = q + 1;
+                double acc = 0.0;
+                for (int j = 0; j < K; ++j) acc = fma(A[j * ld + n + q], d_mono(l, tx[j], ty[j]), acc);
+                err = fmax(err, fabs(acc - d_mono(l, -kEx[k] * dq, -kEy[k] * dq)));
+            }
+            for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+            bad = !(err <= 1e-8);
+        }
+        if (bad && lane == 0) atomicAdd(a.nbad, 1ULL);
+        for (int e = lane; e < 8 * K; e += 32) {
+            int q = e / K, j = e - q * K;
+            double v = bad ? 0.0 : A[j * ld + n + q];
+            int64_t off = sd.w_off + ((int64_t)q * K + j) * sd.n + il;
+            if (a.w64) a.w64[off] = v;
+            if (a.w32) a.w32[off] = (float)v;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+int dev_alloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) return MLBM_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? MLBM_ENOMEM : MLBM_ECUDA,
+                    std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+    }
+    return MLBM_OK;
+}
+
+int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MLBM_OK;
+    return fail(MLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void free_weights(mlbm_weights *w) {
+    if (!w) return;
+    for (auto &kv : w->graphs) cudaGraphExecDestroy((cudaGraphExec_t)kv.second);
+    w->graphs.clear();
+    cudaFree(w->d_seg);
+    cudaFree(w->d_tiles);
+    cudaFree(w->d_idx);
+    cudaFree(w->d_w32);
+    cudaFree(w->d_w64);
+    cudaFree(w->d_mask);
+    cudaFree(w->d_fdir32);
+    cudaFree(w->d_fdir64);
+    cudaFree(w->d_perm);
+    cudaFree(w->d_node_seg);
+    cudaFree(w->d_csr_ptr);
+    cudaFree(w->d_csr_ent);
+    cudaFree(w->d_scratch);
+    cudaFree(w->d_partials);
+    cudaFree(w->d_params);
+    delete w;
+}
+
+}  // namespace
+
+// Solve all systems of a weights object (device arrays must be in place).  Returns the number
+// of bad systems through nbad_out.
+int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStream_t st,
+                  int warps_per_block, int64_t *nbad_out) {
+    int nmax = 0;
+    for (auto &s : w->seg) nmax = std::max(nmax, s.K + s.m);
+    const int ld = (nmax + 8) | 1;
+    const int slot = nmax * ld + 2 * kMaxK;
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
+    if (warps_per_block < 1) warps_per_block = 4;
+    while (warps_per_block > 1 && (size_t)warps_per_block * slot * sizeof(double) > (size_t)maxsm)
+        warps_per_block >>= 1;
+    size_t smem = (size_t)warps_per_block * slot * sizeof(double);
+    if (smem > (size_t)maxsm) return fail(MLBM_EINVAL, "collocation system too large for shared memory");
+    int rc = cuda_check(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem),
+                        "cudaFuncSetAttribute(solve)");
+    if (rc) return rc;
+    unsigned long long *d_bad = nullptr;
+    if ((rc = dev_alloc(&d_bad, 1, "bad counter"))) return rc;
+    cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
+    SolveArgs a;
+    a.seg = w->d_seg;
+    a.x = d_x;
+    a.y = d_y;
+    a.idx = w->d_idx;
+    a.node_seg = w->d_node_seg;
+    a.w64 = w->d_w64;
+    a.w32 = w->d_w32;
+    a.nbad = d_bad;
+    a.N = w->N;
+    a.slot = slot;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, 32 * warps_per_block, smem);
+    int64_t need = (w->N + warps_per_block - 1) / warps_per_block;
+    int64_t grid = std::min<int64_t>(need, (int64_t)std::max(1, per_sm) * w->num_sms);
+    solve_kernel<<<(unsigned)grid, 32 * warps_per_block, smem, st>>>(a);
+    rc = cuda_check(cudaGetLastError(), "solve_kernel launch");
+    unsigned long long nbad = 0;
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(&nbad, d_bad, sizeof(nbad), cudaMemcpyDeviceToHost, st), "copy");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "solve_kernel");
+    cudaFree(d_bad);
+    if (nbad_out) *nbad_out = (int64_t)nbad;
+    return rc;
+}
+
+}  // namespace mlbm
+
+using namespace mlbm;
+
+namespace {
+
+int upload_monomial_tables() {
+    signed char px[64] = {0}, py[64] = {0};
+    int c = 0;
+    for (int t = 0; t <= kMaxDegree; ++t)
+        for (int b = 0; b <= t; ++b) {
+            px[c] = (signed char)(t - b);
+            py[c] = (signed char)b;
+            ++c;
+        }
+    cudaError_t e = cudaMemcpyToSymbol(c_mono_px, px, sizeof(px));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_mono_py, py, sizeof(py));
+    return e == cudaSuccess ? MLBM_OK : fail(MLBM_ECUDA, std::string("monomial tables: ") + cudaGetErrorString(e));
+}
+
+template <typename T>
+int upload(T **dst, const T *src, size_t count, const char *what) {
+    int rc = dev_alloc(dst, count, what);
+    if (rc) return rc;
+    if (count == 0) return MLBM_OK;
+    return cuda_check(cudaMemcpy(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice), what);
+}
+
+}  // namespace
+
+namespace mlbm {
+int tile_nodes_default() { return 256; }
+void prepare_step_grids(mlbm_weights *w);
+}
+
+extern "C" {
+
+int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weights **out,
+                       int64_t *n_bad) {
+    set_error("");
+    if (!c || !out) return fail(MLBM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (flags == 0) flags = MLBM_KEEP_W32 | MLBM_KEEP_W64;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MLBM_ECUDA, "no usable CUDA device");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    mlbm_weights *w = new (std::nothrow) mlbm_weights();
+    if (!w) return fail(MLBM_ENOMEM, "host allocation failed");
+    w->device = dev;
+    cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    w->nseg = c->nseg;
+    w->N = c->N;
+    w->seg = c->seg;
+    w->perm = c->perm;
+    w->idx_total = c->idx_total;
+    w->w_total = c->w_total;
+    w->tile_nodes = tile_nodes_default();
+    int rc = upload_monomial_tables();
+    // segment table
+    std::vector<SegDev> sd(c->nseg);
+    for (int s = 0; s < c->nseg; ++s) {
+        const SegmentHost &h = c->seg[s];
+        sd[s].off = h.off;
+        sd[s].n = h.n;
+        sd[s].idx_off = h.idx_off;
+        sd[s].w_off = h.w_off;
+        sd[s].K = h.K;
+        sd[s].m = h.m;
+        sd[s].deg = h.d.degree;
+        sd[s].geometry = h.d.geometry;
+        sd[s].lx = h.d.lx;
+        sd[s].ly = h.d.ly;
+        sd[s].dx_ml = h.d.dx_ml;
+        sd[s].pad = 0;
+    }
+    // tiles: contiguous runs of tile_nodes stored nodes within one segment, largest stencils first
+    std::vector<TileDev> tiles;
+    for (int s = 0; s < c->nseg; ++s) {
+        const SegmentHost &h = c->seg[s];
+        for (int64_t b = 0; b < h.n; b += w->tile_nodes) {
+            TileDev t;
+            t.begin = h.off + b;
+            t.count = (int32_t)std::min<int64_t>(w->tile_nodes, h.n - b);
+            t.seg = s;
+            tiles.push_back(t);
+        }
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &p, const TileDev &q) {
+        return c->seg[p.seg].K > c->seg[q.seg].K;
+    });
+    w->ntiles = (int)tiles.size();
+    bool any_mask = false;
+    for (auto m : c->mask) any_mask |= (m != 0);
+    w->has_mask = any_mask;
+    std::vector<float> fd32(c->fdir.begin(), c->fdir.end());
+    double *d_x = nullptr, *d_y = nullptr;
+    if (!rc) rc = upload(&w->d_seg, sd.data(), sd.size(), "segments");
+    if (!rc) rc = upload(&w->d_tiles, tiles.data(), tiles.size(), "tiles");
+    if (!rc) rc = upload(&w->d_idx, c->idx.data(), c->idx.size(), "stencil");
+    if (!rc) rc = upload(&w->d_mask, c->mask.data(), c->mask.size(), "mask");
+    if (!rc) rc = upload(&w->d_fdir64, c->fdir.data(), c->fdir.size(), "force direction");
+    if (!rc) rc = upload(&w->d_fdir32, fd32.data(), fd32.size(), "force direction");
+    if (!rc) rc = upload(&w->d_perm, c->perm.data(), c->perm.size(), "permutation");
+    if (!rc) rc = upload(&w->d_node_seg, c->node_seg.data(), c->node_seg.size(), "node segments");
+    if (!rc) rc = upload(&w->d_csr_ptr, c->csr_ptr.data(), c->csr_ptr.size(), "transposed stencil");
+    if (!rc) rc = upload(&w->d_csr_ent, c->csr_ent.data(), c->csr_ent.size(), "transposed stencil");
+    if (!rc) rc = upload(&d_x, c->x.data(), c->x.size(), "x");
+    if (!rc) rc = upload(&d_y, c->y.data(), c->y.size(), "y");
+    if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64, (size_t)w->w_total, "W64");
+    if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32, (size_t)w->w_total, "W32");
+    if (!rc) rc = dev_alloc(&w->d_params, (size_t)4 * c->nseg, "params");
+    int64_t nbad = 0;
+    if (!rc) rc = solve_weights(w, d_x, d_y, st, 4, &nbad);
+    cudaFree(d_x);
+    cudaFree(d_y);
+    if (rc) {
+        free_weights(w);
+        return rc;
+    }
+    prepare_step_grids(w);
+    if (n_bad) *n_bad = nbad;
+    *out = w;
+    if (nbad > 0)
+        return fail(MLBM_ESINGULAR, std::to_string(nbad) + " collocation systems singular or inaccurate");
+    return MLBM_OK;
+}
+
+void mlbm_weights_free(mlbm_weights *w) { free_weights(w); }
+
+int mlbm_weights_info(const mlbm_weights *w, int64_t *n_nodes, int *nseg) {
+    if (!w) return fail(MLBM_EINVAL, "NULL weights");
+    if (n_nodes) *n_nodes = w->N;
+    if (nseg) *nseg = w->nseg;
+    return MLBM_OK;
+}
+
+int mlbm_weights_download(const mlbm_weights *w, int seg, double *W) {
+    if (!w || !W) return fail(MLBM_EINVAL, "NULL argument");
+    if (seg < 0 || seg >= w->nseg) return fail(MLBM_EINVAL, "segment out of range");
+    if (!w->d_w64) return fail(MLBM_EINVAL, "weights were built without MLBM_KEEP_W64");
+    const SegmentHost &h = w->seg[seg];
+    size_t cnt = (size_t)8 * h.K * h.n;
+    std::vector<double> tmp(cnt);
+    int rc = cuda_check(cudaMemcpy(tmp.data(), w->d_w64 + h.w_off, cnt * sizeof(double), cudaMemcpyDeviceToHost),
+                        "download weights");
+    if (rc) return rc;
+    for (int64_t p = 0; p < h.n; ++p) {
+        int64_t io = w->perm[h.off + p] - h.orig_off;
+        for (int64_t r = 0; r < (int64_t)8 * h.K; ++r) W[r * h.n + io] = tmp[r * h.n + p];
+    }
+    return MLBM_OK;
+}
+
+int mlbm_weights_upload(mlbm_weights *w, int seg, const double *W, const int32_t *idx) {
+    if (!w || !W || !idx) return fail(MLBM_EINVAL, "NULL argument");
+    if (seg < 0 || seg >= w->nseg) return fail(MLBM_EINVAL, "segment out of range");
+    const SegmentHost &h = w->seg[seg];
+    // check the caller's stencil against ours (original numbering)
+    std::vector<int32_t> own((size_t)h.K * h.n);
+    int rc = cuda_check(cudaMemcpy(own.data(), w->d_idx + h.idx_off, own.size() * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost),
+                        "download stencil");
+    if (rc) return rc;
+    for (int j = 0; j < h.K; ++j)
+        for (int64_t p = 0; p < h.n; ++p) {
+            int64_t io = w->perm[h.off + p] - h.orig_off;
+            int64_t member = w->perm[own[(size_t)j * h.n + p]] - h.orig_off;
+            if (idx[(int64_t)j * h.n + io] != member)
+                return fail(MLBM_EINVAL, "stencil differs from the library's stencil");
+        }
+    size_t cnt = (size_t)8 * h.K * h.n;
+    std::vector<double> tmp(cnt);
+    for (int64_t p = 0; p < h.n; ++p) {
+        int64_t io = w->perm[h.off + p] - h.orig_off;
+        for (int64_t r = 0; r < (int64_t)8 * h.K; ++r) tmp[r * h.n + p] = W[r * h.n + io];
+    }
+    if (w->d_w64)
+        if ((rc = cuda_check(cudaMemcpy(w->d_w64 + h.w_off, tmp.data(), cnt * sizeof(double), cudaMemcpyHostToDevice),
+                             "upload weights")))
+            return rc;
+    if (w->d_w32) {
+        std::vector<float> t32(tmp.begin(), tmp.end());
+        if ((rc = cuda_check(cudaMemcpy(w->d_w32 + h.w_off, t32.data(), cnt * sizeof(float), cudaMemcpyHostToDevice),
+                             "upload weights")))
+            return rc;
+    }
+    return MLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated here, derived in the design notes):
+  * FP64 step with shared shape vectors: <= 1e-12 relative per step (max |diff| / max |f|).
+  * shape vectors, GPU vs oracle (both LU with partial pivoting in FP64 on the same matrix):
+    <= WEIGHT_TOL absolute (|w| is O(1); the systems are ill-conditioned, so the two
+    factorisations agree to about cond(Phi) * eps rather than eps).
+  * FP32 deviation-storage path: <= 1e-6 relative L2 of the velocity after the run.
+"""
+import numpy as np
+import pytest
+
+import mlbm_inputs as mi
+import oracle
+
+torch = pytest.importorskip("torch")
+mlbm = pytest.importorskip("paper_2306_01525_gb300")
+
+pytestmark = pytest.mark.gpu
+
+WEIGHT_TOL = {2: 1e-9, 3: 1e-8, 4: 1e-7}
+STEP_TOL = 1e-12
+FP32_TOL = 1e-6
+
+
+def _dev():
+    return torch.device("cuda:0")
+
+
+def _periodic(k, deg, dx):
+    return dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=k, degree=deg, dx_ml=dx)
+
+
+def _setup_tgv(n_side, K, deg, ratio=1.0, seed=1, jitter=0.3):
+    xy = mi.jittered_lattice(n_side, jitter, seed=seed) if jitter > 0 else mi.lattice(n_side)
+    dx = ratio / n_side
+    seg = _periodic(K, deg, dx)
+    cloud = mlbm.build_cloud(xy, seg)
+    w = mlbm.build_weights(cloud)
+    return xy, dx, cloud, w
+
+
+def _to_orig(w_stored, perm):
+    """[c][N] stored order -> original order."""
+    out = np.empty_like(w_stored)
+    out[:, perm] = w_stored
+    return out
+
+
+def _gpu_init(w, params, dtype, rho, u, v):
+    td = torch.float32 if dtype == mlbm.F32 else torch.float64
+    f = torch.empty(9 * w.n, dtype=td, device=_dev())
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=_dev()).contiguous()
+    mlbm.init(w, params, dtype, t(rho), t(u), t(v), f)
+    return f
+
+
+def _upload_oracle_weights(w, xy, K, deg, dx, box=(1.0, 1.0)):
+    sidx, W = oracle.weights(xy, K, deg, dx, box=box)
+    w.upload(W[1:], sidx[1].astype(np.int32))
+    return sidx, W
+
+
+# ----------------------------------------------------------------------------- shape vectors
+
+@pytest.mark.parametrize("n_side,K,deg", [(32, 12, 2), (24, 16, 3), (20, 30, 4)])
+def test_weights_match_oracle(n_side, K, deg):
+    xy, dx, cloud, w = _setup_tgv(n_side, K, deg)
+    assert w.n_bad == 0
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0))
+    np.testing.assert_array_equal(cloud.stencil(0), sidx[1])
+    Wg = w.download(0)
+    err = np.max(np.abs(Wg - W[1:]))
+    assert err <= WEIGHT_TOL[deg], err
+
+
+@pytest.mark.parametrize("K,deg", [(12, 2), (30, 4), (45, 6)])
+def test_gpu_weights_reproduce_polynomials(K, deg):
+    """Property check independent of the oracle: sum_j w_j p(x_j) = p(departure point)."""
+    n_side = 24
+    xy, dx, cloud, w = _setup_tgv(n_side, K, deg)
+    Wg = w.download(0)
+    st = cloud.stencil(0)
+    ex = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    for i in range(0, xy.shape[1], 37):
+        d = xy[:, st[:, i]] - xy[:, i:i + 1]
+        d -= np.round(d)
+        s = np.max(np.hypot(d[0], d[1]))
+        t = d / s
+        for k in range(1, 9):
+            q = np.array([-ex[k] * dx, -ey[k] * dx]) / s
+            for a in range(deg + 1):
+                for b in range(deg + 1 - a):
+                    got = np.sum(Wg[k - 1, :, i] * t[0] ** a * t[1] ** b)
+                    assert abs(got - q[0] ** a * q[1] ** b) < 1e-9
+
+
+# ----------------------------------------------------------------------------- FP64 step
+
+@pytest.mark.parametrize("n_side,K,deg,ratio", [(32, 12, 2, 1.0), (20, 30, 4, 1.0), (17, 16, 3, 0.5)])
+def test_fp64_step_matches_oracle_per_step(n_side, K, deg, ratio):
+    """Shared (oracle) shape vectors uploaded to the GPU: every step agrees to 1e-12."""
+    xy, dx, cloud, w = _setup_tgv(n_side, K, deg, ratio=ratio)
+    sidx, W = _upload_oracle_weights(w, xy, K, deg, dx)
+    tau = 0.8
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01 * ratio)
+    perm = cloud.perm()
+    f_or = oracle.init_equilibrium(rho, u, v)
+    st = oracle.Stepper(sidx, W, tau)
+    fa = _gpu_init(w, params, mlbm.F64, rho, u, v)
+    fb = torch.empty_like(fa)
+    mom = torch.empty(3 * w.n, dtype=torch.float64, device=_dev())
+    n = w.n
+    post = oracle.collide_field(f_or, tau)
+    got = _to_orig(fa.view(9, n).cpu().numpy(), perm)
+    assert np.max(np.abs(got - post)) <= STEP_TOL * np.max(np.abs(post))
+    for it in range(12):
+        mlbm.step(w, params, mlbm.F64, fa, fb, mom)
+        fa, fb = fb, fa
+        f_or = st.step(f_or)
+        post = oracle.collide_field(f_or, tau)
+        got = _to_orig(fa.view(9, n).cpu().numpy(), perm)
+        rel = np.max(np.abs(got - post)) / np.max(np.abs(post))
+        assert rel <= STEP_TOL, (it, rel)
+        r_o, u_o, v_o = oracle.moments_field(f_or)
+        m = _to_orig(mom.view(3, n).cpu().numpy(), perm)
+        np.testing.assert_allclose(m[0], r_o, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(m[1], u_o, rtol=0, atol=1e-14)
+        np.testing.assert_allclose(m[2], v_o, rtol=0, atol=1e-14)
+
+
+def test_moments_entry_point_matches_oracle():
+    xy, dx, cloud, w = _setup_tgv(16, 12, 2)
+    _upload_oracle_weights(w, xy, 12, 2, dx)
+    params = [(0.8, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.02)
+    for dtype in (mlbm.F64, mlbm.F32):
+        f = _gpu_init(w, params, dtype, rho, u, v)
+        r, uu, vv = mlbm.moments(w, params, dtype, f)
+        tol = 1e-15 if dtype == mlbm.F64 else 1e-8
+        np.testing.assert_allclose(r.cpu().numpy(), rho, atol=tol * 10)
+        np.testing.assert_allclose(uu.cpu().numpy(), u, atol=tol)
+        np.testing.assert_allclose(vv.cpu().numpy(), v, atol=tol)
+
+
+def test_fp64_run_own_weights_matches_oracle_run():
+    """Configuration of the small Taylor-Green workload: 32^2 jittered, N_L = 12, P_2,
+    tau = 0.8, u0 = 0.01, 500 steps; each side with its own shape vectors."""
+    xy, dx, cloud, w = _setup_tgv(32, 12, 2)
+    tau, steps = 0.8, 500
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01)
+    sidx, W = oracle.weights(xy, 12, 2, dx, box=(1.0, 1.0))
+    f_or = oracle.Stepper(sidx, W, tau).run(oracle.init_equilibrium(rho, u, v), steps)
+    _, u_o, v_o = oracle.moments_field(f_or)
+    fa = _gpu_init(w, params, mlbm.F64, rho, u, v)
+    fb = torch.empty_like(fa)
+    res = mlbm.run(w, params, mlbm.F64, fa, fb, steps)
+    _, ug, vg = mlbm.moments(w, params, mlbm.F64, res)
+    ug, vg = ug.cpu().numpy(), vg.cpu().numpy()
+    err = np.sqrt(np.sum((ug - u_o) ** 2 + (vg - v_o) ** 2) / np.sum(u_o ** 2 + v_o ** 2))
+    assert err <= 1e-9, err
+    # and the physics: close to the analytic Taylor-Green decay
+    nu = oracle.lattice_viscosity(tau)
+    ut, _ = oracle.tgv_velocity(xy[0] / dx, xy[1] / dx, steps, u0=0.01, nu=nu, L=1.0 / dx)
+    assert oracle.l2_norm(ug, ut) < 0.05
+
+
+# ----------------------------------------------------------------------------- FP32 path
+
+@pytest.mark.parametrize("n_side,K,deg,steps", [(32, 12, 2, 500), (20, 30, 4, 300)])
+def test_fp32_run_within_1e6_of_fp64_oracle(n_side, K, deg, steps):
+    xy, dx, cloud, w = _setup_tgv(n_side, K, deg)
+    tau = 0.8
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01)
+    sidx, W = _upload_oracle_weights(w, xy, K, deg, dx)
+    f_or = oracle.Stepper(sidx, W, tau).run(oracle.init_equilibrium(rho, u, v), steps)
+    _, u_o, v_o = oracle.moments_field(f_or)
+    fa = _gpu_init(w, params, mlbm.F32, rho, u, v)
+    fb = torch.empty_like(fa)
+    res = mlbm.run(w, params, mlbm.F32, fa, fb, steps)
+    _, ug, vg = mlbm.moments(w, params, mlbm.F32, res)
+    ug, vg = ug.cpu().numpy(), vg.cpu().numpy()
+    err = np.sqrt(np.sum((ug - u_o) ** 2 + (vg - v_o) ** 2) / np.sum(u_o ** 2 + v_o ** 2))
+    assert err <= FP32_TOL, err
+
+
+# ----------------------------------------------------------------------------- annulus
+
+def _setup_annulus(h, K, deg, dx, seed=3):
+    xy, wall = mi.annulus_cloud(h=h, seed=seed)
+    seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=K, degree=deg, dx_ml=dx)
+    cloud = mlbm.build_cloud(xy, seg)
+    w = mlbm.build_weights(cloud)
+    return xy, cloud, w
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_annulus_step_with_force_and_bounce_back_matches_oracle(dtype):
+    dx = 1.0 / 40
+    K, deg, tau, g = 15, 2, 1.0, 1e-5
+    xy, cloud, w = _setup_annulus(mi.ANNULUS_H_FOR[1000], K, deg, dx)
+    sidx, W = oracle.weights(xy, K, deg, dx)
+    w.upload(W[1:], sidx[1].astype(np.int32))
+    mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
+    assert np.array_equal(cloud.bounce_mask(), mask) and mask.any()
+    force = oracle.azimuthal_force(xy, g)
+    st = oracle.Stepper(sidx, W, tau, mask=mask, force=force)
+    n = xy.shape[1]
+    rng = np.random.default_rng(0)
+    rho = 1.0 + 1e-3 * rng.standard_normal(n)
+    u = 1e-3 * rng.standard_normal(n)
+    v = 1e-3 * rng.standard_normal(n)
+    params = [(tau, g, 1.0)]
+    dt = mlbm.F64 if dtype == "f64" else mlbm.F32
+    fa = _gpu_init(w, params, dt, rho, u, v)
+    fb = torch.empty_like(fa)
+    f_or = oracle.init_equilibrium(rho, u, v)
+    perm = cloud.perm()
+    steps = 30
+    for it in range(steps):
+        mlbm.step(w, params, dt, fa, fb)
+        fa, fb = fb, fa
+        f_or = st.step(f_or)
+        if dtype == "f64":
+            post = oracle.collide_field(f_or, tau, force)
+            got = _to_orig(fa.view(9, n).cpu().numpy(), perm)
+            assert np.max(np.abs(got - post)) <= STEP_TOL * np.max(np.abs(post)), it
+    r_g, u_g, v_g = mlbm.moments(w, params, dt, fa)
+    r_o, u_o, v_o = oracle.moments_field(f_or)
+    tol = 1e-13 if dtype == "f64" else 2e-7
+    np.testing.assert_allclose(r_g.cpu().numpy(), r_o, atol=tol)
+    np.testing.assert_allclose(u_g.cpu().numpy(), u_o, atol=tol * 1e-1)
+    np.testing.assert_allclose(v_g.cpu().numpy(), v_o, atol=tol * 1e-1)
+
+
+# ----------------------------------------------------------------------------- batching
+
+def test_batched_segments_match_single_runs_and_oracle():
+    cases = [(16, 12, 2, 1.0, 0.8), (20, 16, 3, 0.5, 0.7), (12, 24, 4, 0.25, 1.1), (9, 8, 1, 1.0, 0.9)]
+    parts, segs, params = [], [], []
+    for s, (ns, K, deg, ratio, tau) in enumerate(cases):
+        parts.append(mi.jittered_lattice(ns, 0.3, seed=70 + s))
+        segs.append(_periodic(K, deg, ratio / ns))
+        params.append((tau, 0.0, 1.0))
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    cloud = mlbm.build_cloud(xy, segs, offs)
+    w = mlbm.build_weights(cloud)
+    rho = np.ones(xy.shape[1])
+    u = np.concatenate([mi.tgv_initial(p, 0.01)[1] for p in parts])
+    v = np.concatenate([mi.tgv_initial(p, 0.01)[2] for p in parts])
+    fa = _gpu_init(w, params, mlbm.F64, rho, u, v)
+    fb = torch.empty_like(fa)
+    res = mlbm.run(w, params, mlbm.F64, fa, fb, 40)
+    _, ub, vb = mlbm.moments(w, params, mlbm.F64, res)
+    ub = ub.cpu().numpy()
+    for s, p in enumerate(parts):
+        c1 = mlbm.build_cloud(p, segs[s])
+        w1 = mlbm.build_weights(c1)
+        np.testing.assert_array_equal(w1.download(0), w.download(s))
+        _, u1, v1 = mi.tgv_initial(p, 0.01)
+        f1 = _gpu_init(w1, [params[s]], mlbm.F64, np.ones(p.shape[1]), u1, v1)
+        g1 = torch.empty_like(f1)
+        r1 = mlbm.run(w1, [params[s]], mlbm.F64, f1, g1, 40)
+        _, us, _ = mlbm.moments(w1, [params[s]], mlbm.F64, r1)
+        np.testing.assert_array_equal(us.cpu().numpy(), ub[offs[s]:offs[s + 1]])
+        sidx, W = oracle.weights(p, segs[s]["k"], segs[s]["degree"], segs[s]["dx_ml"], box=(1.0, 1.0))
+        err = np.max(np.abs(w.download(s) - W[1:]))
+        assert err <= 1e-7, (s, err)
+
+
+def test_run_graph_equals_repeated_steps():
+    xy, dx, cloud, w = _setup_tgv(24, 12, 2)
+    params = [(0.8, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01)
+    for dtype in (mlbm.F32, mlbm.F64):
+        fa = _gpu_init(w, params, dtype, rho, u, v)
+        fb = torch.empty_like(fa)
+        ga, gb = fa.clone(), torch.empty_like(fa)
+        steps = 131  # two 64-step graph replays plus a tail
+        res = mlbm.run(w, params, dtype, fa, fb, steps)
+        for _ in range(steps):
+            mlbm.step(w, params, dtype, ga, gb)
+            ga, gb = gb, ga
+        assert torch.equal(res, ga)
+
+
+def test_ragged_tail_and_minimal_segment():
+    """N not a multiple of the 256-node tile and a segment with exactly N_L nodes."""
+    parts = [mi.jittered_lattice(31, 0.3, seed=5), mi.jittered_lattice(3, 0.2, seed=6)]
+    segs = [_periodic(12, 2, 1.0 / 31), _periodic(9, 2, 0.1 / 3)]
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    cloud = mlbm.build_cloud(xy, segs, offs)
+    w = mlbm.build_weights(cloud)
+    assert w.n % 256 != 0
+    params = [(0.8, 0.0, 1.0), (0.9, 0.0, 1.0)]
+    rho = np.ones(xy.shape[1])
+    u = np.concatenate([mi.tgv_initial(p, 0.01)[1] for p in parts])
+    v = np.concatenate([mi.tgv_initial(p, 0.01)[2] for p in parts])
+    for s, p in enumerate(parts):
+        sidx, W = oracle.weights(p, segs[s]["k"], 2, segs[s]["dx_ml"], box=(1.0, 1.0))
+        w.upload(W[1:], sidx[1].astype(np.int32), seg=s)
+    fa = _gpu_init(w, params, mlbm.F64, rho, u, v)
+    fb = torch.empty_like(fa)
+    res = mlbm.run(w, params, mlbm.F64, fa, fb, 7)
+    _, ug, _ = mlbm.moments(w, params, mlbm.F64, res)
+    ug = ug.cpu().numpy()
+    for s, p in enumerate(parts):
+        sidx, W = oracle.weights(p, segs[s]["k"], 2, segs[s]["dx_ml"], box=(1.0, 1.0))
+        _, u1, v1 = mi.tgv_initial(p, 0.01)
+        f = oracle.Stepper(sidx, W, params[s][0]).run(
+            oracle.init_equilibrium(np.ones(p.shape[1]), u1, v1), 7)
+        _, uo, _ = oracle.moments_field(f)
+        np.testing.assert_allclose(ug[offs[s]:offs[s + 1]], uo, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- norms, errors
+
+def test_norms_match_numpy():
+    xy, dx, cloud, w = _setup_tgv(8, 9, 2)
+    rng = np.random.default_rng(3)
+    n = 123457
+    a, b, c, d = (rng.standard_normal(n) for _ in range(4))
+    t = lambda z: torch.as_tensor(z, device=_dev())
+    out = mlbm.norms(w, t(a), t(b), t(c), t(d))
+    want = [np.sum((a - b) ** 2 + (c - d) ** 2), np.sum(b ** 2 + d ** 2), np.sum(a ** 2 + c ** 2)]
+    np.testing.assert_allclose(out, want, rtol=1e-13)
+    out1 = mlbm.norms(w, t(a), t(b))
+    np.testing.assert_allclose(out1, [np.sum((a - b) ** 2), np.sum(b ** 2), np.sum(a ** 2)], rtol=1e-13)
+    # deterministic
+    assert np.array_equal(out, mlbm.norms(w, t(a), t(b), t(c), t(d)))
+
+
+def test_step_argument_errors():
+    xy, dx, cloud, w = _setup_tgv(8, 9, 2)
+    f = torch.zeros(9 * w.n, dtype=torch.float64, device=_dev())
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.step(w, [(0.4, 0.0, 1.0)], mlbm.F64, f, f.clone())  # tau <= 1/2
+    assert e.value.code == mlbm.EINVAL
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.step(w, [(0.8, 0.0, 1.0)], mlbm.F64, f, f)  # in place is not allowed
+    assert e.value.code == mlbm.EINVAL
+    w32 = mlbm.build_weights(cloud, keep=mlbm.KEEP_W32)
+    with pytest.raises(mlbm.MLBMError):
+        mlbm.step(w32, [(0.8, 0.0, 1.0)], mlbm.F64, f, f.clone())
+
+
+def test_singular_stencil_reported():
+    """Collinear stencils cannot carry the quadratic monomials: the solver flags them."""
+    x = np.linspace(0.05, 0.95, 12)
+    xy = np.stack([x, np.full(12, 0.5)])
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.ANNULUS, r_in=0.0, r_out=10.0, k=9,
+                                      degree=2, dx_ml=0.01))
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.build_weights(cloud)
+    assert e.value.code == mlbm.ESINGULAR
+    w = mlbm.build_weights(cloud, check=False)
+    assert w.n_bad == 12
