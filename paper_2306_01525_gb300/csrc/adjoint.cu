@@ -67,14 +67,15 @@ struct AdjArgs {
     const SegDev *__restrict__ seg;
     const TileDev *__restrict__ tiles;
     const int32_t *__restrict__ idx;
-    const T *__restrict__ w;
+    const double *__restrict__ w64;  // canonical [8][K][n] per segment
     const uint16_t *__restrict__ mask;
     const T *__restrict__ fdir;
     const double *__restrict__ params;
     const T *__restrict__ s_prev;
     const T *__restrict__ lam_next;
     T *__restrict__ lam_prev;
-    T *__restrict__ mut;  // [8][N] scratch
+    T *__restrict__ mut;    // [8][N] scratch: bounce-back-transposed cotangent of fhat
+    T *__restrict__ selfc;  // [8][N] scratch: centre contribution (1 - sum_{j>=1} w) mut
     double *__restrict__ partials;  // [ntiles][2]
     const int32_t *__restrict__ csr_ptr;
     const int32_t *__restrict__ csr_ent;
@@ -82,6 +83,9 @@ struct AdjArgs {
     int ntiles;
 };
 
+// Local part of the reverse step at every node: recompute fhat (difference-form interpolation of
+// s_prev as in the forward kernel, then bounce-back), apply the transposed collision Jacobian to
+// lam_next, then the transposed bounce-back; accumulate dL/dtau and dL/dg per tile.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
     constexpr bool kDev = std::is_same<T, float>::value;
@@ -90,21 +94,32 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
         double dtau = 0.0, dg = 0.0;
-        if ((int)threadIdx.x < tile.count) {
-            const int64_t p = tile.begin + threadIdx.x;
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+            const int64_t p = tile.begin + b;
             const SegDev &sd = a.seg[tile.seg];
             const int64_t n = sd.n, il = p - sd.off, KN = (int64_t)sd.K * n;
             const int K = sd.K;
-            T f[9];
-            f[0] = a.s_prev[p];
+            T f[9], wsum[9];
 #pragma unroll
-            for (int k = 1; k < 9; ++k) f[k] = T(0);
-            for (int j = 0; j < K; ++j) {
-                const int32_t nb = a.idx[sd.idx_off + (int64_t)j * n + il];
-                const T *wj = a.w + sd.w_off + (int64_t)j * n + il;
-#pragma unroll
-                for (int k = 1; k < 9; ++k) f[k] = fma(wj[(int64_t)(k - 1) * KN], a.s_prev[(int64_t)k * N + nb], f[k]);
+            for (int k = 0; k < 9; ++k) {
+                f[k] = a.s_prev[(int64_t)k * N + p];
+                wsum[k] = T(0);
             }
+            T acc[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc[k] = T(0);
+            for (int j = 1; j < K; ++j) {
+                const int32_t nb = a.idx[sd.idx_off + (int64_t)j * n + il];
+                const double *wj = a.w64 + sd.w_off + (int64_t)j * n + il;
+#pragma unroll
+                for (int k = 1; k < 9; ++k) {
+                    const T wk = (T)wj[(int64_t)(k - 1) * KN];
+                    acc[k] = fma(wk, a.s_prev[(int64_t)k * N + nb] - f[k], acc[k]);
+                    wsum[k] += wk;
+                }
+            }
+#pragma unroll
+            for (int k = 1; k < 9; ++k) f[k] += acc[k];
             const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
             if (mb) {
                 T g[9];
@@ -131,8 +146,8 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                 st += lam[k] * (f[k] - geq);
                 sg += lam[k] * omega_of<T>(k) * T(3) * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
             }
-            dtau = (double)st / ((double)tau * (double)tau);
-            dg = (double)sg;
+            dtau += (double)st / ((double)tau * (double)tau);
+            dg += (double)sg;
             T Ar, Ax, Ay;
             feq_vjp<T>(lam, rho, ux, uy, Ar, Ax, Ay);
             const T ir = T(1) / rho;
@@ -151,7 +166,10 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
             }
             a.lam_prev[p] = mt[0];
 #pragma unroll
-            for (int k = 1; k < 9; ++k) a.mut[(int64_t)(k - 1) * N + p] = mt[k];
+            for (int k = 1; k < 9; ++k) {
+                a.mut[(int64_t)(k - 1) * N + p] = mt[k];
+                a.selfc[(int64_t)(k - 1) * N + p] = (T(1) - wsum[k]) * mt[k];
+            }
         }
         block_sum2(dtau, dg, sh);
         if (threadIdx.x == 0) {
@@ -161,29 +179,32 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
     }
 }
 
-// lam_prev_k(m) = sum over (i, j) with s_j(i) = m of W_k[j](i) mut_k(i), k = 1..8.
+// lam_prev_k(m) = (1 - sum_{j>=1} W_k[j](m)) mut_k(m) + sum over (i, j >= 1) with s_j(i) = m of
+// W_k[j](i) mut_k(i), k = 1..8: the transpose of the difference-form interpolation.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
     const int64_t N = a.N;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
-        if ((int)threadIdx.x >= tile.count) continue;
-        const int64_t mnode = tile.begin + threadIdx.x;
-        const SegDev &sd = a.seg[tile.seg];
-        const int64_t n = sd.n, KN = (int64_t)sd.K * n;
-        T acc[8];
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+            const int64_t mnode = tile.begin + b;
+            const SegDev &sd = a.seg[tile.seg];
+            const int64_t n = sd.n, KN = (int64_t)sd.K * n;
+            T acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = T(0);
-        const int32_t b = a.csr_ptr[mnode], e = a.csr_ptr[mnode + 1];
-        for (int32_t q = b; q < e; ++q) {
-            const int32_t ent = a.csr_ent[q];
-            const int64_t i = sd.off + (int64_t)(ent % n);
-            const T *wq = a.w + sd.w_off + ent;
+            for (int k = 0; k < 8; ++k) acc[k] = a.selfc[(int64_t)k * N + mnode];
+            const int32_t e0 = a.csr_ptr[mnode], e1 = a.csr_ptr[mnode + 1];
+            for (int32_t q = e0; q < e1; ++q) {
+                const int32_t ent = a.csr_ent[q];
+                if (ent < n) continue;  // member 0: the node itself, counted in selfc
+                const int64_t i = sd.off + (int64_t)(ent % n);
+                const double *wq = a.w64 + sd.w_off + ent;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = fma(wq[(int64_t)k * KN], a.mut[(int64_t)k * N + i], acc[k]);
+                for (int k = 0; k < 8; ++k) acc[k] = fma((T)wq[(int64_t)k * KN], a.mut[(int64_t)k * N + i], acc[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + mnode] = acc[k];
         }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + mnode] = acc[k];
     }
 }
 
@@ -218,8 +239,8 @@ __global__ void __launch_bounds__(kThreads) moments_adjoint_kernel(
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
         double dg = 0.0, zero = 0.0;
-        if ((int)threadIdx.x < tile.count) {
-            const int64_t p = tile.begin + threadIdx.x;
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+            const int64_t p = tile.begin + b;
             const double *pr = params + 4 * tile.seg;
             double s[9];
 #pragma unroll
@@ -234,7 +255,7 @@ __global__ void __launch_bounds__(kThreads) moments_adjoint_kernel(
 #pragma unroll
             for (int l = 0; l < 9; ++l)
                 lam[(int64_t)l * N + p] = (T)(a + (bx * (ex_of(l) - ux) + by * (ey_of(l) - uy)) / rho);
-            dg = -(bx * fx + by * fy) / rho;
+            dg += -(bx * fx + by * fy) / rho;
         }
         block_sum2(zero, dg, sh);
         if (threadIdx.x == 0) {
@@ -255,8 +276,8 @@ __global__ void __launch_bounds__(kThreads) init_adjoint_kernel(
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
         double dg = 0.0, zero = 0.0;
-        if ((int)threadIdx.x < tile.count) {
-            const int64_t p = tile.begin + threadIdx.x;
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+            const int64_t p = tile.begin + b;
             const int64_t o = perm[p];
             double lam[9];
 #pragma unroll
@@ -279,7 +300,7 @@ __global__ void __launch_bounds__(kThreads) init_adjoint_kernel(
 }
 
 int ensure_adj_scratch(mlbm_weights *w) {
-    size_t need = sizeof(double) * (8 * (size_t)w->N + 2 * (size_t)w->ntiles);
+    size_t need = sizeof(double) * (16 * (size_t)w->N + 2 * (size_t)w->ntiles);
     if (w->d_scratch && w->scratch_bytes >= need) return MLBM_OK;
     cudaFree(w->d_scratch);
     w->d_scratch = nullptr;
@@ -307,7 +328,7 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *lam_next, vo
     a.seg = w->d_seg;
     a.tiles = w->d_tiles;
     a.idx = w->d_idx;
-    a.w = std::is_same<T, float>::value ? (const T *)w->d_w32 : (const T *)w->d_w64;
+    a.w64 = w->d_w64;
     a.mask = w->has_mask ? w->d_mask : nullptr;
     a.fdir = std::is_same<T, float>::value ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
     a.params = w->d_params;
@@ -315,7 +336,8 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *lam_next, vo
     a.lam_next = (const T *)lam_next;
     a.lam_prev = (T *)lam_prev;
     a.mut = (T *)w->d_scratch;
-    a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 8 * (size_t)w->N);
+    a.selfc = (T *)w->d_scratch + 8 * (size_t)w->N;
+    a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 16 * (size_t)w->N);
     a.csr_ptr = w->d_csr_ptr;
     a.csr_ent = w->d_csr_ent;
     a.N = w->N;
@@ -360,7 +382,7 @@ int mlbm_moments_adjoint(const mlbm_weights *w, const mlbm_params *params, int d
     int rc = set_params(wm, params, st);
     if (rc) return rc;
     if ((rc = ensure_adj_scratch(wm))) return rc;
-    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 8 * (size_t)w->N);
+    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 16 * (size_t)w->N);
     if (dtype == MLBM_F32)
         moments_adjoint_kernel<float><<<grid_of(w, (const void *)moments_adjoint_kernel<float>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params, (const float *)f, drho, dux, duy, (float *)lam,
@@ -385,7 +407,7 @@ int mlbm_init_adjoint(const mlbm_weights *w, const mlbm_params *params, int dtyp
     int rc = set_params(wm, params, st);
     if (rc) return rc;
     if ((rc = ensure_adj_scratch(wm))) return rc;
-    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 8 * (size_t)w->N);
+    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 16 * (size_t)w->N);
     if (dtype == MLBM_F32)
         init_adjoint_kernel<float><<<grid_of(w, (const void *)init_adjoint_kernel<float>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, rho, ux, uy, (const float *)lam0, drho, dux, duy, partials,

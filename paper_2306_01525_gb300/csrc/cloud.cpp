@@ -2,6 +2,7 @@
 // bounce-back): Morton reorder, grid-bucket k-nearest neighbours, bounce-back masks, force
 // directions and the transposed stencil used by the adjoint.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -308,13 +309,20 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
             const int64_t *orig = &c->perm[o];
             int K = sh.K;
             int32_t *idx = &c->idx[sh.idx_off];
+            std::atomic<int> dup{0};
             parallel_for(ns, [&](int64_t b, int64_t e) {
                 int32_t tmp[kMaxK];
                 for (int64_t i = b; i < e; ++i) {
                     knn_query(g, sxp, syp, orig, i, K, tmp);
+                    if (tmp[0] != (int32_t)i) dup = 1;
                     for (int j = 0; j < K; ++j) idx[(int64_t)j * ns + i] = (int32_t)(o + tmp[j]);
                 }
             });
+            if (dup.load()) {
+                delete c;
+                return fail(MLBM_EINVAL, "duplicate nodes in segment " + std::to_string(s) +
+                                             " (a node must be the first member of its own stencil)");
+            }
             // bounce-back mask and force direction (Sec. 3)
             for (int64_t i = 0; i < ns; ++i) {
                 double xx = sxp[i], yy = syp[i];

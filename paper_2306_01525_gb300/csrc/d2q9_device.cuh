@@ -63,4 +63,33 @@ __device__ __forceinline__ void collide(T (&s)[9], T rho_ref, T inv_tau, T gx, T
     }
 }
 
+// FP32 collision with exact conservation by construction.  With rounded lattice weights
+// (fl(1/9), fl(1/36)) the equilibrium's mass and momentum differ from those of fhat by a fixed
+// relative amount (3 (2 omega_1 + 4 omega_5) = 1 + 2.2e-8 in FP32), which would rescale the
+// momentum of every node identically at every step.  The non-equilibrium part n = fhat - f^eq
+// is therefore projected onto zero mass and momentum with exact operations (its mass is taken
+// from n_0, half of its x / y momentum from each of n_1, n_3 / n_2, n_4) before relaxing.
+__device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, float inv_tau, float gx, float gy,
+                                                  float &rho, float &ux, float &uy) {
+    float drho;
+    moments_of(s, rho_ref, drho, rho, ux, uy);
+    const float usq15 = 1.5f * (ux * ux + uy * uy);
+    float ne[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) ne[k] = s[k] - geq_of<float>(k, drho, rho, ux, uy, usq15);
+    const float dm = ((ne[0] + ne[1]) + (ne[2] + ne[3])) + ((ne[4] + ne[5]) + (ne[6] + ne[7])) + ne[8];
+    const float dx = (ne[1] - ne[3]) + (ne[5] - ne[6]) + (ne[8] - ne[7]);
+    const float dy = (ne[2] - ne[4]) + (ne[5] + ne[6]) - (ne[7] + ne[8]);
+    ne[0] -= dm;
+    ne[1] -= 0.5f * dx;
+    ne[3] += 0.5f * dx;
+    ne[2] -= 0.5f * dy;
+    ne[4] += 0.5f * dy;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float force = omega_of<float>(k) * 3.0f * (float(ex_of(k)) * gx + float(ey_of(k)) * gy);
+        s[k] = s[k] - ne[k] * inv_tau + force;
+    }
+}
+
 }  // namespace mlbm

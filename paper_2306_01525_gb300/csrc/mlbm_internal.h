@@ -56,11 +56,21 @@ struct SegDev {
     double lx, ly, dx_ml, pad;
 };
 
+// Nodes per tile of the fused step: one CTA pass over a contiguous Morton run.
+constexpr int kTileNodes = 512;
+
 // A tile: a contiguous run of stored nodes of one segment processed by one CTA pass.
+// Its halo (the tile's own nodes first, then every other node its stencils read, sorted) is
+// staged in shared memory; the stencil members are 16-bit slots into that halo.
 struct TileDev {
     int64_t begin;  // first stored position
+    int64_t w_off;  // element offset of the tile's shape vectors in the tile layouts
+    int64_t l_off;  // offset of the tile's packed slot pairs ([ceil((K-1)/2)][kTileNodes] uint32)
+    int64_t h_off;  // offset of the tile's halo list (int32 stored positions)
     int32_t count;  // nodes in tile
     int32_t seg;    // segment index
+    int32_t K;      // stencil size of the segment
+    int32_t U;      // halo size (slots)
 };
 
 struct GraphKey {
@@ -84,8 +94,13 @@ struct mlbm_weights_impl {
     int ntiles = 0;
     int tile_nodes = 0;
     int32_t *d_idx = nullptr;
-    float *d_w32 = nullptr;
-    double *d_w64 = nullptr;
+    double *d_w64 = nullptr;    // canonical FP64 shape vectors, per segment [8][K][n]
+    float *d_w32t = nullptr;    // tile layout, FP32: [j-1][2][kTileNodes][4 directions]
+    double *d_w64t = nullptr;   // tile layout, FP64: [j-1][4][kTileNodes][2 directions]
+    uint32_t *d_lidx = nullptr; // packed 16-bit halo slots of stencil members 1..K-1
+    int32_t *d_halo = nullptr;  // halo lists
+    int umax = 0;               // largest halo of any tile
+    int64_t wt_total = 0, l_total = 0, h_total = 0;
     uint16_t *d_mask = nullptr;
     float *d_fdir32 = nullptr;
     double *d_fdir64 = nullptr;

@@ -29,10 +29,10 @@ namespace {
 
 template <typename T>
 struct StepArgs {
-    const SegDev *__restrict__ seg;
     const TileDev *__restrict__ tiles;
-    const int32_t *__restrict__ idx;
-    const T *__restrict__ w;
+    const int32_t *__restrict__ halo;
+    const uint32_t *__restrict__ lidx;
+    const T *__restrict__ wt;           // tile layout shape vectors
     const uint16_t *__restrict__ mask;  // NULL when no segment has wall populations
     const T *__restrict__ fdir;         // [2][N]
     const double *__restrict__ params;  // [nseg][4]: tau, g, rho0, unused
@@ -43,63 +43,144 @@ struct StepArgs {
     int ntiles;
 };
 
+// Populations moved per shared-memory or shape-vector load: 4 directions in FP32 (16 B),
+// 2 directions in FP64 (16 B).
+template <typename T> struct V;
+template <> struct V<float> {
+    using type = float4;
+    static constexpr int width = 4;
+};
+template <> struct V<double> {
+    using type = double2;
+    static constexpr int width = 2;
+};
+
+__device__ __forceinline__ void vfma(float4 &acc, const float4 w, const float4 x, const float4 c) {
+    acc.x = fmaf(w.x, x.x - c.x, acc.x);
+    acc.y = fmaf(w.y, x.y - c.y, acc.y);
+    acc.z = fmaf(w.z, x.z - c.z, acc.z);
+    acc.w = fmaf(w.w, x.w - c.w, acc.w);
+}
+__device__ __forceinline__ void vfma(double2 &acc, const double2 w, const double2 x, const double2 c) {
+    acc.x = fma(w.x, x.x - c.x, acc.x);
+    acc.y = fma(w.y, x.y - c.y, acc.y);
+}
+__device__ __forceinline__ void vzero(float4 &v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void vzero(double2 &v) { v = make_double2(0.0, 0.0); }
+__device__ __forceinline__ void vpack(float4 &v, const float *s) { v = make_float4(s[0], s[1], s[2], s[3]); }
+__device__ __forceinline__ void vpack(double2 &v, const double *s) { v = make_double2(s[0], s[1]); }
+__device__ __forceinline__ void vunpack_sum(float *d, const float4 &c, const float4 &a) {
+    d[0] = c.x + a.x;
+    d[1] = c.y + a.y;
+    d[2] = c.z + a.z;
+    d[3] = c.w + a.w;
+}
+__device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const double2 &a) {
+    d[0] = c.x + a.x;
+    d[1] = c.y + a.y;
+}
+
+// One fused time step over all tiles (persistent CTAs, one node per thread, kTileNodes threads):
+//   1. stage f^post_k (k = 1..8) of the tile's halo in shared memory as [slot][8];
+//   2. fhat_k(i) = f_k(i) + sum_{j>=1} W_k[j](i) (f_k(s_j(i)) - f_k(i))  -- the shape vector
+//      sums to one (constant reproduction), so the centre weight is implied and never loaded;
+//   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
 template <typename T>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs<T> a) {
-    constexpr bool kDev = std::is_same<T, float>::value;
+__global__ void __launch_bounds__(kTileNodes, (sizeof(T) == 4 ? 2 : 1)) step_kernel(StepArgs<T> a) {
+    using VT = typename V<T>::type;
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;  // vectors per 8 moving populations
+    constexpr int B = kTileNodes;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     const int64_t N = a.N;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
-        if ((int)threadIdx.x >= tile.count) continue;
-        const int64_t p = tile.begin + threadIdx.x;
-        const SegDev &sd = a.seg[tile.seg];
-        const int64_t n = sd.n;
-        const int K = sd.K;
-        const int64_t il = p - sd.off;
-        const int32_t *__restrict__ ip = a.idx + sd.idx_off + il;
-        const T *__restrict__ wp = a.w + sd.w_off + il;
-        const int64_t KN = (int64_t)K * n;
-        T f[9];
-        f[0] = a.fin[p];
+        // 1. halo staging (own nodes first, then the other members sorted: mostly coalesced)
+        for (int u = threadIdx.x; u < tile.U; u += blockDim.x) {
+            const int64_t node = __ldg(a.halo + tile.h_off + u);
+            T v[8];
 #pragma unroll
-        for (int k = 1; k < 9; ++k) f[k] = T(0);
-        // pull-stream: fhat_k(i) = sum_j W_k[j](i) f^post_k(s_j(i))
-#pragma unroll 2
-        for (int j = 0; j < K; ++j) {
-            const int32_t nb = __ldg(ip + (int64_t)j * n);
-            const T *__restrict__ wj = wp + (int64_t)j * n;
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(a.fin + (int64_t)(k + 1) * N + node);
 #pragma unroll
-            for (int k = 1; k < 9; ++k) f[k] = fma(__ldg(wj + (int64_t)(k - 1) * KN), __ldg(a.fin + (int64_t)k * N + nb), f[k]);
+            for (int q = 0; q < NV; ++q) vpack(sh[u * NV + q], v + q * W);
         }
-        // wall bounce-back: unknown populations take the streamed opposite population
-        if (a.mask) {
-            const uint16_t mb = a.mask[p];
-            if (mb) {
-                T g[9];
+        __syncthreads();
+        const int b = threadIdx.x;
+        if (b < tile.count) {
+            const int64_t p = tile.begin + b;
+            VT c[NV], acc[NV];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) g[k] = f[k];
+            for (int q = 0; q < NV; ++q) {
+                c[q] = sh[b * NV + q];
+                vzero(acc[q]);
+            }
+            const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+            const VT *__restrict__ wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+            const int m1 = tile.K - 1;  // stencil members 1..K-1
+            int j = 0;
+            // 2. interpolation, two members per packed slot word
+#pragma unroll 2
+            for (; j + 1 < m1; j += 2) {
+                const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
+                VT w0[NV], w1[NV];
 #pragma unroll
-                for (int k = 1; k < 9; ++k)
-                    if (mb >> k & 1u) f[k] = g[opp_of(k)];
+                for (int q = 0; q < NV; ++q) {
+                    w0[q] = __ldcs(wp + (int64_t)(j * NV + q) * B);
+                    w1[q] = __ldcs(wp + (int64_t)((j + 1) * NV + q) * B);
+                }
+                const int s0 = (int)(pr & 0xFFFFu), s1 = (int)(pr >> 16);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vfma(acc[q], w0[q], sh[s0 * NV + q], c[q]);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vfma(acc[q], w1[q], sh[s1 * NV + q], c[q]);
+            }
+            if (j < m1) {
+                const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
+                const int s0 = (int)(pr & 0xFFFFu);
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vfma(acc[q], __ldcs(wp + (int64_t)(j * NV + q) * B), sh[s0 * NV + q], c[q]);
+            }
+            T f[9];
+            f[0] = a.fin[p];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+            // 3. wall bounce-back: unknown populations take the streamed opposite population
+            if (a.mask) {
+                const uint16_t mb = a.mask[p];
+                if (mb) {
+                    T g[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) g[k] = f[k];
+#pragma unroll
+                    for (int k = 1; k < 9; ++k)
+                        if (mb >> k & 1u) f[k] = g[opp_of(k)];
+                }
+            }
+            // 4. collision
+            const double *pr = a.params + 4 * tile.seg;
+            const T inv_tau = T(1.0 / pr[0]);
+            const T gm = T(pr[1]);
+            T gx = T(0), gy = T(0);
+            if (gm != T(0)) {
+                gx = gm * a.fdir[p];
+                gy = gm * a.fdir[N + p];
+            }
+            T rho, ux, uy;
+            if constexpr (std::is_same<T, float>::value)
+                collide_projected(f, T(pr[2]), inv_tau, gx, gy, rho, ux, uy);
+            else
+                collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
+            // 5. store
+#pragma unroll
+            for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
+            if (a.mom) {
+                a.mom[p] = rho;
+                a.mom[N + p] = ux;
+                a.mom[2 * N + p] = uy;
             }
         }
-        const double *pr = a.params + 4 * tile.seg;
-        const T inv_tau = T(1.0 / pr[0]);
-        const T gm = T(pr[1]);
-        const T rho_ref = kDev ? T(pr[2]) : T(0);
-        T gx = T(0), gy = T(0);
-        if (gm != T(0)) {
-            gx = gm * a.fdir[p];
-            gy = gm * a.fdir[N + p];
-        }
-        T rho, ux, uy;
-        collide<T>(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
-        if (a.mom) {
-            a.mom[p] = rho;
-            a.mom[N + p] = ux;
-            a.mom[2 * N + p] = uy;
-        }
+        __syncthreads();
     }
 }
 
@@ -112,8 +193,8 @@ __global__ void init_kernel(const TileDev *__restrict__ tiles, int ntiles, const
     constexpr bool kDev = std::is_same<T, float>::value;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
-        if ((int)threadIdx.x >= tile.count) continue;
-        const int64_t p = tile.begin + threadIdx.x;
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+        const int64_t p = tile.begin + b;
         const int64_t o = perm[p];
         const double *pr = params + 4 * tile.seg;
         const double rho_ref = kDev ? pr[2] : 0.0;
@@ -125,6 +206,7 @@ __global__ void init_kernel(const TileDev *__restrict__ tiles, int ntiles, const
             double s = geq_of<double>(k, rho - rho_ref, rho, ux, uy, usq15) +
                        omega_of<double>(k) * 3.0 * (ex_of(k) * gx + ey_of(k) * gy);
             f[(int64_t)k * N + p] = (T)s;
+        }
         }
     }
 }
@@ -139,8 +221,8 @@ __global__ void moments_kernel(const TileDev *__restrict__ tiles, int ntiles, co
     constexpr bool kDev = std::is_same<T, float>::value;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
-        if ((int)threadIdx.x >= tile.count) continue;
-        const int64_t p = tile.begin + threadIdx.x;
+        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+        const int64_t p = tile.begin + b;
         const double *pr = params + 4 * tile.seg;
         double s[9];
 #pragma unroll
@@ -154,6 +236,7 @@ __global__ void moments_kernel(const TileDev *__restrict__ tiles, int ntiles, co
         rho_out[o] = rho;
         ux_out[o] = ux;
         uy_out[o] = uy;
+        }
     }
 }
 
@@ -241,18 +324,25 @@ int set_params(mlbm_weights *w, const mlbm_params *params, cudaStream_t st) {
 }
 
 int check_dtype(const mlbm_weights *w, int dtype) {
-    if (dtype == MLBM_F32) return w->d_w32 ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
-    if (dtype == MLBM_F64) return w->d_w64 ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W64");
+    if (dtype == MLBM_F32)
+        return (w->d_w32t && w->step_grid[0]) ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
+    if (dtype == MLBM_F64)
+        return (w->d_w64t && w->step_grid[1]) ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W64");
     return fail(MLBM_EINVAL, "dtype must be MLBM_F32 or MLBM_F64");
+}
+
+template <typename T>
+size_t step_smem(const mlbm_weights *w) {
+    return (size_t)w->umax * 8 * sizeof(T);
 }
 
 template <typename T>
 int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom, cudaStream_t st) {
     StepArgs<T> a;
-    a.seg = w->d_seg;
     a.tiles = w->d_tiles;
-    a.idx = w->d_idx;
-    a.w = std::is_same<T, float>::value ? (const T *)w->d_w32 : (const T *)w->d_w64;
+    a.halo = w->d_halo;
+    a.lidx = w->d_lidx;
+    a.wt = std::is_same<T, float>::value ? (const T *)w->d_w32t : (const T *)w->d_w64t;
     a.mask = w->has_mask ? w->d_mask : nullptr;
     a.fdir = std::is_same<T, float>::value ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
     a.params = w->d_params;
@@ -262,14 +352,28 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.N = w->N;
     a.ntiles = w->ntiles;
     const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
-    step_kernel<T><<<grid, 256, 0, st>>>(a);
+    step_kernel<T><<<grid, kTileNodes, step_smem<T>(w), st>>>(a);
     return cuda_check_step(cudaGetLastError(), "step_kernel launch");
 }
 
 // Persistent grids of the step kernels: CTAs resident per SM x SMs, capped by the tile count.
-void prepare_step_grids(mlbm_weights *w) {
-    w->step_grid[0] = grid_for(w, (const void *)step_kernel<float>, 256, 0);
-    w->step_grid[1] = grid_for(w, (const void *)step_kernel<double>, 256, 0);
+// A precision whose halo does not fit in shared memory gets grid 0 and is refused by the step.
+int prepare_step_grids(mlbm_weights *w) {
+    const void *fns[2] = {(const void *)step_kernel<float>, (const void *)step_kernel<double>};
+    const size_t sm[2] = {step_smem<float>(w), step_smem<double>(w)};
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
+    for (int i = 0; i < 2; ++i) {
+        w->step_grid[i] = 0;
+        if (sm[i] > (size_t)maxsm) continue;
+        int rc = cuda_check_step(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[i]),
+                                 "step shared-memory attribute");
+        if (rc) return rc;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], kTileNodes, sm[i]);
+        w->step_grid[i] = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
+    }
+    return MLBM_OK;
 }
 
 int launch_step(const mlbm_weights *w, int dtype, const void *fin, void *fout, void *mom, cudaStream_t st) {

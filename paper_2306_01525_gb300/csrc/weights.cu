@@ -55,8 +55,7 @@ struct SolveArgs {
     const double *x, *y;
     const int32_t *idx;
     const int32_t *node_seg;
-    double *w64;
-    float *w32;
+    double *w64;  // canonical [8][K][n] per segment
     unsigned long long *nbad;
     int64_t N;
     int slot;  // doubles per warp slot
@@ -189,10 +188,45 @@ __global__ void solve_kernel(SolveArgs a) {
             int q = e / K, j = e - q * K;
             double v = bad ? 0.0 : A[j * ld + n + q];
             int64_t off = sd.w_off + ((int64_t)q * K + j) * sd.n + il;
-            if (a.w64) a.w64[off] = v;
-            if (a.w32) a.w32[off] = (float)v;
+            a.w64[off] = v;
         }
         __syncwarp();
+    }
+}
+
+// Canonical [8][K][n] FP64 shape vectors -> tile layouts of the fused step (members 1..K-1):
+//   FP32: element (((j-1) * 2 + h) * kTileNodes + b) * 4 + r, direction k = 1 + 4 h + r
+//   FP64: element (((j-1) * 4 + q) * kTileNodes + b) * 2 + r, direction k = 1 + 2 q + r
+__global__ void repack_kernel(const TileDev *__restrict__ tiles, int ntiles, const SegDev *__restrict__ seg,
+                              const double *__restrict__ w64c, float *__restrict__ w32t,
+                              double *__restrict__ w64t) {
+    constexpr int B = kTileNodes;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const TileDev tile = tiles[t];
+        const SegDev &sd = seg[tile.seg];
+        const int K = tile.K;
+        const int64_t il0 = tile.begin - sd.off;
+        const int64_t total = (int64_t)(K - 1) * 8 * B;
+        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+            if (w32t) {
+                const int r = (int)(e & 3);
+                const int64_t q4 = e >> 2;
+                const int b = (int)(q4 % B);
+                const int64_t jh = q4 / B;
+                const int h = (int)(jh & 1), j = (int)(jh >> 1) + 1, k = 1 + 4 * h + r;
+                double v = b < tile.count ? w64c[sd.w_off + ((int64_t)(k - 1) * K + j) * sd.n + il0 + b] : 0.0;
+                w32t[tile.w_off + e] = (float)v;
+            }
+            if (w64t) {
+                const int r = (int)(e & 1);
+                const int64_t q2 = e >> 1;
+                const int b = (int)(q2 % B);
+                const int64_t jq = q2 / B;
+                const int q = (int)(jq & 3), j = (int)(jq >> 2) + 1, k = 1 + 2 * q + r;
+                double v = b < tile.count ? w64c[sd.w_off + ((int64_t)(k - 1) * K + j) * sd.n + il0 + b] : 0.0;
+                w64t[tile.w_off + e] = v;
+            }
+        }
     }
 }
 
@@ -222,8 +256,11 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_seg);
     cudaFree(w->d_tiles);
     cudaFree(w->d_idx);
-    cudaFree(w->d_w32);
     cudaFree(w->d_w64);
+    cudaFree(w->d_w32t);
+    cudaFree(w->d_w64t);
+    cudaFree(w->d_lidx);
+    cudaFree(w->d_halo);
     cudaFree(w->d_mask);
     cudaFree(w->d_fdir32);
     cudaFree(w->d_fdir64);
@@ -268,7 +305,6 @@ int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStr
     a.idx = w->d_idx;
     a.node_seg = w->d_node_seg;
     a.w64 = w->d_w64;
-    a.w32 = w->d_w32;
     a.nbad = d_bad;
     a.N = w->N;
     a.slot = slot;
@@ -285,6 +321,19 @@ int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStr
     if (nbad_out) *nbad_out = (int64_t)nbad;
     return rc;
 }
+
+// Refresh the tile layouts from the canonical FP64 shape vectors.
+int repack_weights(mlbm_weights *w, cudaStream_t st) {
+    if (!w->d_w32t && !w->d_w64t) return MLBM_OK;
+    int grid = std::max(1, std::min(w->ntiles, 8 * w->num_sms));
+    repack_kernel<<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_seg, w->d_w64, w->d_w32t, w->d_w64t);
+    int rc = cuda_check(cudaGetLastError(), "repack launch");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "repack");
+    return rc;
+}
+
+int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
+                std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total);
 
 }  // namespace mlbm
 
@@ -317,8 +366,7 @@ int upload(T **dst, const T *src, size_t count, const char *what) {
 }  // namespace
 
 namespace mlbm {
-int tile_nodes_default() { return 256; }
-void prepare_step_grids(mlbm_weights *w);
+int prepare_step_grids(mlbm_weights *w);
 }
 
 extern "C" {
@@ -345,7 +393,7 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     w->perm = c->perm;
     w->idx_total = c->idx_total;
     w->w_total = c->w_total;
-    w->tile_nodes = tile_nodes_default();
+    w->tile_nodes = kTileNodes;
     int rc = upload_monomial_tables();
     // segment table
     std::vector<SegDev> sd(c->nseg);
@@ -364,21 +412,17 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
         sd[s].dx_ml = h.d.dx_ml;
         sd[s].pad = 0;
     }
-    // tiles: contiguous runs of tile_nodes stored nodes within one segment, largest stencils first
+    // tiles of the fused step with their halos and packed stencil slots
     std::vector<TileDev> tiles;
-    for (int s = 0; s < c->nseg; ++s) {
-        const SegmentHost &h = c->seg[s];
-        for (int64_t b = 0; b < h.n; b += w->tile_nodes) {
-            TileDev t;
-            t.begin = h.off + b;
-            t.count = (int32_t)std::min<int64_t>(w->tile_nodes, h.n - b);
-            t.seg = s;
-            tiles.push_back(t);
-        }
+    std::vector<int32_t> halo;
+    std::vector<uint32_t> lidx;
+    if (!rc) rc = build_tiles(c, tiles, halo, lidx, w->umax, w->wt_total);
+    if (rc) {
+        free_weights(w);
+        return rc;
     }
-    std::stable_sort(tiles.begin(), tiles.end(), [&](const TileDev &p, const TileDev &q) {
-        return c->seg[p.seg].K > c->seg[q.seg].K;
-    });
+    w->l_total = (int64_t)lidx.size();
+    w->h_total = (int64_t)halo.size();
     w->ntiles = (int)tiles.size();
     bool any_mask = false;
     for (auto m : c->mask) any_mask |= (m != 0);
@@ -397,18 +441,25 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     if (!rc) rc = upload(&w->d_csr_ent, c->csr_ent.data(), c->csr_ent.size(), "transposed stencil");
     if (!rc) rc = upload(&d_x, c->x.data(), c->x.size(), "x");
     if (!rc) rc = upload(&d_y, c->y.data(), c->y.size(), "y");
-    if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64, (size_t)w->w_total, "W64");
-    if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32, (size_t)w->w_total, "W32");
+    if (!rc) rc = upload(&w->d_halo, halo.data(), halo.size(), "halo lists");
+    if (!rc) rc = upload(&w->d_lidx, lidx.data(), lidx.size(), "stencil slots");
+    if (!rc) rc = dev_alloc(&w->d_w64, (size_t)w->w_total, "W64");
+    if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64t, (size_t)w->wt_total, "W64 tiles");
+    if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32t, (size_t)w->wt_total, "W32 tiles");
     if (!rc) rc = dev_alloc(&w->d_params, (size_t)4 * c->nseg, "params");
     int64_t nbad = 0;
     if (!rc) rc = solve_weights(w, d_x, d_y, st, 4, &nbad);
+    if (!rc) rc = repack_weights(w, st);
     cudaFree(d_x);
     cudaFree(d_y);
     if (rc) {
         free_weights(w);
         return rc;
     }
-    prepare_step_grids(w);
+    if ((rc = prepare_step_grids(w))) {
+        free_weights(w);
+        return rc;
+    }
     if (n_bad) *n_bad = nbad;
     *out = w;
     if (nbad > 0)
@@ -428,7 +479,6 @@ int mlbm_weights_info(const mlbm_weights *w, int64_t *n_nodes, int *nseg) {
 int mlbm_weights_download(const mlbm_weights *w, int seg, double *W) {
     if (!w || !W) return fail(MLBM_EINVAL, "NULL argument");
     if (seg < 0 || seg >= w->nseg) return fail(MLBM_EINVAL, "segment out of range");
-    if (!w->d_w64) return fail(MLBM_EINVAL, "weights were built without MLBM_KEEP_W64");
     const SegmentHost &h = w->seg[seg];
     size_t cnt = (size_t)8 * h.K * h.n;
     std::vector<double> tmp(cnt);
@@ -465,16 +515,10 @@ int mlbm_weights_upload(mlbm_weights *w, int seg, const double *W, const int32_t
         int64_t io = w->perm[h.off + p] - h.orig_off;
         for (int64_t r = 0; r < (int64_t)8 * h.K; ++r) tmp[r * h.n + p] = W[r * h.n + io];
     }
-    if (w->d_w64)
-        if ((rc = cuda_check(cudaMemcpy(w->d_w64 + h.w_off, tmp.data(), cnt * sizeof(double), cudaMemcpyHostToDevice),
-                             "upload weights")))
-            return rc;
-    if (w->d_w32) {
-        std::vector<float> t32(tmp.begin(), tmp.end());
-        if ((rc = cuda_check(cudaMemcpy(w->d_w32 + h.w_off, t32.data(), cnt * sizeof(float), cudaMemcpyHostToDevice),
-                             "upload weights")))
-            return rc;
-    }
+    if ((rc = cuda_check(cudaMemcpy(w->d_w64 + h.w_off, tmp.data(), cnt * sizeof(double), cudaMemcpyHostToDevice),
+                         "upload weights")))
+        return rc;
+    if ((rc = repack_weights(w, nullptr))) return rc;
     return MLBM_OK;
 }
 
