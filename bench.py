@@ -45,11 +45,12 @@ CPU_SAMPLE = dict(n_side=128, K=30, deg=4, tau=0.8, u0=0.01, seed=3)
 
 
 def step_bytes_per_node(K: int, dtype_bytes: int) -> int:
-    """Algorithmic bytes of one node update: the shape-vector entries of the K - 1 stencil
-    members other than the node itself for the 8 moving directions (the centre weight follows
-    from constant reproduction), K - 1 int32 stencil indices, and the nine populations read
-    once and written once."""
-    return 8 * (K - 1) * dtype_bytes + 4 * (K - 1) + 2 * 9 * dtype_bytes
+    """Algorithmic bytes of one node update: the shape-vector entries of the 8 moving
+    directions (FP32: the K - 1 members other than the node itself, whose centre weight follows
+    from constant reproduction; FP64: all K members, the literal sum), K - 1 int32 stencil
+    indices, and the nine populations read once and written once."""
+    members = K - 1 if dtype_bytes == 4 else K
+    return 8 * members * dtype_bytes + 4 * (K - 1) + 2 * 9 * dtype_bytes
 
 
 def _peaks():

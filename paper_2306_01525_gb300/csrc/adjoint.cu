@@ -3,7 +3,9 @@
 // respect to tau, the body force g and the initial fields.
 //
 // Forward step (storage form s, lattice units): fhat = B (S s), s' = C(fhat; tau, g) with
-//   S  the interpolation fhat_k(i) = sum_j W_k[j](i) s_k(s_j(i))       (Sec. 2.3)
+//   S  the interpolation fhat_k(i) = sum_j W_k[j](i) s_k(s_j(i))       (Sec. 2.3), in the form
+//      the forward kernel evaluates it: FP64 literally, FP32 as s_k(i) + sum_{j>=1} W (s_k(s_j) -
+//      s_k(i)), i.e. with centre coefficient 1 - sum_{j>=1} W_k[j](i)
 //   B  the wall bounce-back fhat_k = fhat_k' on unknown populations      (Sec. 3)
 //   C  the BGK collision with forcing                                    (eq. LBM_collision, Sec. 3)
 // Reverse: mu = J_C^T lam, mut = B^T mu, lam_prev = S^T mut.  S^T is done as a pull over the
@@ -118,8 +120,20 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                     wsum[k] += wk;
                 }
             }
+            if constexpr (kDev) {
+                // FP32 forward: difference form, centre coefficient 1 - sum_{j>=1} w
 #pragma unroll
-            for (int k = 1; k < 9; ++k) f[k] += acc[k];
+                for (int k = 1; k < 9; ++k) f[k] += acc[k];
+            } else {
+                // FP64 forward: literal form, centre coefficient w_0
+                const double *w0 = a.w64 + sd.w_off + il;
+#pragma unroll
+                for (int k = 1; k < 9; ++k) {
+                    const T c0 = (T)w0[(int64_t)(k - 1) * KN];
+                    f[k] = c0 * f[k] + (acc[k] + wsum[k] * f[k]);
+                    wsum[k] = T(1) - c0;
+                }
+            }
             const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
             if (mb) {
                 T g[9];

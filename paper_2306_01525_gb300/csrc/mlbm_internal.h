@@ -64,7 +64,8 @@ constexpr int kTileNodes = 512;
 // staged in shared memory; the stencil members are 16-bit slots into that halo.
 struct TileDev {
     int64_t begin;  // first stored position
-    int64_t w_off;  // element offset of the tile's shape vectors in the tile layouts
+    int64_t w_off;    // element offset of the tile's FP32 shape vectors (members 1..K-1)
+    int64_t w64_off;  // element offset of the tile's FP64 shape vectors (members 0..K-1)
     int64_t l_off;  // offset of the tile's packed slot pairs ([ceil((K-1)/2)][kTileNodes] uint32)
     int64_t h_off;  // offset of the tile's halo list (int32 stored positions)
     int32_t count;  // nodes in tile
@@ -95,12 +96,12 @@ struct mlbm_weights_impl {
     int tile_nodes = 0;
     int32_t *d_idx = nullptr;
     double *d_w64 = nullptr;    // canonical FP64 shape vectors, per segment [8][K][n]
-    float *d_w32t = nullptr;    // tile layout, FP32: [j-1][2][kTileNodes][4 directions]
-    double *d_w64t = nullptr;   // tile layout, FP64: [j-1][4][kTileNodes][2 directions]
+    float *d_w32t = nullptr;    // tile layout, FP32: [j-1][2][kTileNodes][4 directions], j = 1..K-1
+    double *d_w64t = nullptr;   // tile layout, FP64: [j][4][kTileNodes][2 directions], j = 0..K-1
     uint32_t *d_lidx = nullptr; // packed 16-bit halo slots of stencil members 1..K-1
     int32_t *d_halo = nullptr;  // halo lists
     int umax = 0;               // largest halo of any tile
-    int64_t wt_total = 0, l_total = 0, h_total = 0;
+    int64_t wt_total = 0, wt64_total = 0, l_total = 0, h_total = 0;
     uint16_t *d_mask = nullptr;
     float *d_fdir32 = nullptr;
     double *d_fdir64 = nullptr;
@@ -119,6 +120,7 @@ struct mlbm_weights_impl {
     std::vector<double> params_cache;
     int num_sms = 0;
     int step_grid[2] = {0, 0};  // persistent grid of the step kernel, [FP32, FP64]
+    int solve_wpb = 0;          // warps per CTA the solver ran with (autotuned)
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
 };

@@ -55,15 +55,39 @@ template <> struct V<double> {
     static constexpr int width = 2;
 };
 
+// acc += w (x - c) (difference form, FP32) or acc += w x (literal form, FP64)
+template <bool kLiteral>
 __device__ __forceinline__ void vfma(float4 &acc, const float4 w, const float4 x, const float4 c) {
     acc.x = fmaf(w.x, x.x - c.x, acc.x);
     acc.y = fmaf(w.y, x.y - c.y, acc.y);
     acc.z = fmaf(w.z, x.z - c.z, acc.z);
     acc.w = fmaf(w.w, x.w - c.w, acc.w);
 }
+template <bool kLiteral>
 __device__ __forceinline__ void vfma(double2 &acc, const double2 w, const double2 x, const double2 c) {
-    acc.x = fma(w.x, x.x - c.x, acc.x);
-    acc.y = fma(w.y, x.y - c.y, acc.y);
+    if constexpr (kLiteral) {
+        acc.x = fma(w.x, x.x, acc.x);
+        acc.y = fma(w.y, x.y, acc.y);
+    } else {
+        acc.x = fma(w.x, x.x - c.x, acc.x);
+        acc.y = fma(w.y, x.y - c.y, acc.y);
+    }
+}
+__device__ __forceinline__ void vmul(float4 &acc, const float4 w, const float4 x) {
+    acc = make_float4(w.x * x.x, w.y * x.y, w.z * x.z, w.w * x.w);
+}
+__device__ __forceinline__ void vmul(double2 &acc, const double2 w, const double2 x) {
+    acc = make_double2(w.x * x.x, w.y * x.y);
+}
+__device__ __forceinline__ void vunpack(float *d, const float4 &a) {
+    d[0] = a.x;
+    d[1] = a.y;
+    d[2] = a.z;
+    d[3] = a.w;
+}
+__device__ __forceinline__ void vunpack(double *d, const double2 &a) {
+    d[0] = a.x;
+    d[1] = a.y;
 }
 __device__ __forceinline__ void vzero(float4 &v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ void vzero(double2 &v) { v = make_double2(0.0, 0.0); }
@@ -82,12 +106,15 @@ __device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const d
 
 // One fused time step over all tiles (persistent CTAs, one node per thread, kTileNodes threads):
 //   1. stage f^post_k (k = 1..8) of the tile's halo in shared memory as [slot][8];
-//   2. fhat_k(i) = f_k(i) + sum_{j>=1} W_k[j](i) (f_k(s_j(i)) - f_k(i))  -- the shape vector
-//      sums to one (constant reproduction), so the centre weight is implied and never loaded;
+//   2. FP32: fhat_k(i) = f_k(i) + sum_{j>=1} W_k[j](i) (f_k(s_j(i)) - f_k(i)) -- the shape vector
+//      sums to one (constant reproduction), so the centre weight is implied and never loaded,
+//      and rounding of the FP32 weights only touches the small differences;
+//      FP64: fhat_k(i) = sum_{j>=0} W_k[j](i) f_k(s_j(i)) as written in eq. (shape_vector);
 //   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
 template <typename T>
 __global__ void __launch_bounds__(kTileNodes, (sizeof(T) == 4 ? 2 : 1)) step_kernel(StepArgs<T> a) {
     using VT = typename V<T>::type;
+    constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;  // vectors per 8 moving populations
     constexpr int B = kTileNodes;
@@ -116,7 +143,16 @@ __global__ void __launch_bounds__(kTileNodes, (sizeof(T) == 4 ? 2 : 1)) step_ker
                 vzero(acc[q]);
             }
             const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
-            const VT *__restrict__ wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+            const VT *__restrict__ wp;
+            if constexpr (kLiteral) {
+                // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
+                wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
+                wp += (int64_t)NV * B;
+            } else {
+                wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+            }
             const int m1 = tile.K - 1;  // stencil members 1..K-1
             int j = 0;
             // 2. interpolation, two members per packed slot word
@@ -131,20 +167,26 @@ __global__ void __launch_bounds__(kTileNodes, (sizeof(T) == 4 ? 2 : 1)) step_ker
                 }
                 const int s0 = (int)(pr & 0xFFFFu), s1 = (int)(pr >> 16);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma(acc[q], w0[q], sh[s0 * NV + q], c[q]);
+                for (int q = 0; q < NV; ++q) vfma<kLiteral>(acc[q], w0[q], sh[s0 * NV + q], c[q]);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma(acc[q], w1[q], sh[s1 * NV + q], c[q]);
+                for (int q = 0; q < NV; ++q) vfma<kLiteral>(acc[q], w1[q], sh[s1 * NV + q], c[q]);
             }
             if (j < m1) {
                 const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
                 const int s0 = (int)(pr & 0xFFFFu);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma(acc[q], __ldcs(wp + (int64_t)(j * NV + q) * B), sh[s0 * NV + q], c[q]);
+                for (int q = 0; q < NV; ++q)
+                    vfma<kLiteral>(acc[q], __ldcs(wp + (int64_t)(j * NV + q) * B), sh[s0 * NV + q], c[q]);
             }
             T f[9];
             f[0] = a.fin[p];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+            for (int q = 0; q < NV; ++q) {
+                if constexpr (kLiteral)
+                    vunpack(f + 1 + q * W, acc[q]);
+                else
+                    vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+            }
             // 3. wall bounce-back: unknown populations take the streamed opposite population
             if (a.mask) {
                 const uint16_t mb = a.mask[p];

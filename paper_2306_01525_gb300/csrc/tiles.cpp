@@ -12,9 +12,9 @@
 namespace mlbm {
 
 int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
-                std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total) {
+                std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total, int64_t &wt64_total) {
     tiles.clear();
-    int64_t w_off = 0, l_off = 0;
+    int64_t w_off = 0, w64_off = 0, l_off = 0;
     for (int s = 0; s < c->nseg; ++s) {
         const SegmentHost &h = c->seg[s];
         for (int64_t b = 0; b < h.n; b += kTileNodes) {
@@ -24,13 +24,16 @@ int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<in
             t.seg = s;
             t.K = h.K;
             t.w_off = w_off;
+            t.w64_off = w64_off;
             t.l_off = l_off;
             w_off += (int64_t)(h.K - 1) * 8 * kTileNodes;
+            w64_off += (int64_t)h.K * 8 * kTileNodes;
             l_off += (int64_t)((h.K - 1 + 1) / 2) * kTileNodes;
             tiles.push_back(t);
         }
     }
     wt_total = w_off;
+    wt64_total = w64_off;
     lidx.assign((size_t)l_off, 0u);
     const int nt = (int)tiles.size();
     std::vector<std::vector<int32_t>> halos(nt);

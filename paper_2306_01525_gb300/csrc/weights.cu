@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -154,9 +156,26 @@ __global__ void solve_kernel(SolveArgs a) {
             const double inv = 1.0 / A[p * ld + p];
             for (int r = p + 1 + lane; r < n; r += 32) A[r * ld + p] *= inv;
             __syncwarp();
+            // trailing update A[r][c] -= l_r A[p][c], rows in groups of four with all loads issued
+            // before the stores (shared memory aliasing would otherwise serialise every row)
             for (int c = p + 1 + lane; c < nc; c += 32) {
                 const double apc = A[p * ld + c];
-                for (int r = p + 1; r < n; ++r) A[r * ld + c] = fma(-A[r * ld + p], apc, A[r * ld + c]);
+                int r = p + 1;
+                for (; r + 3 < n; r += 4) {
+                    const double l0 = A[r * ld + p], l1 = A[(r + 1) * ld + p];
+                    const double l2 = A[(r + 2) * ld + p], l3 = A[(r + 3) * ld + p];
+                    double a0 = A[r * ld + c], a1 = A[(r + 1) * ld + c];
+                    double a2 = A[(r + 2) * ld + c], a3 = A[(r + 3) * ld + c];
+                    a0 = fma(-l0, apc, a0);
+                    a1 = fma(-l1, apc, a1);
+                    a2 = fma(-l2, apc, a2);
+                    a3 = fma(-l3, apc, a3);
+                    A[r * ld + c] = a0;
+                    A[(r + 1) * ld + c] = a1;
+                    A[(r + 2) * ld + c] = a2;
+                    A[(r + 3) * ld + c] = a3;
+                }
+                for (; r < n; ++r) A[r * ld + c] = fma(-A[r * ld + p], apc, A[r * ld + c]);
             }
             __syncwarp();
         }
@@ -165,10 +184,19 @@ __global__ void solve_kernel(SolveArgs a) {
             for (int p = n - 1; p >= 0; --p) {
                 if (lane < 8) A[p * ld + n + lane] /= A[p * ld + p];
                 __syncwarp();
-                for (int t = lane; t < p * 8; t += 32) {
-                    int r = t >> 3, q = t & 7;
-                    A[r * ld + n + q] = fma(-A[r * ld + p], A[p * ld + n + q], A[r * ld + n + q]);
+                // lanes over (row, rhs) pairs; rows r = lane/8, lane/8 + 4, ... (four per pass)
+                const int q = lane & 7;
+                const double zq = A[p * ld + n + q];
+                int r = lane >> 3;
+                for (; r + 4 < p; r += 8) {
+                    const double l0 = A[r * ld + p], l1 = A[(r + 4) * ld + p];
+                    double a0 = A[r * ld + n + q], a1 = A[(r + 4) * ld + n + q];
+                    a0 = fma(-l0, zq, a0);
+                    a1 = fma(-l1, zq, a1);
+                    A[r * ld + n + q] = a0;
+                    A[(r + 4) * ld + n + q] = a1;
                 }
+                for (; r < p; r += 4) A[r * ld + n + q] = fma(-A[r * ld + p], zq, A[r * ld + n + q]);
                 __syncwarp();
             }
             // polynomial reproduction check: sum_j w_j p_l(x_j) = p_l(q_k)
@@ -194,9 +222,9 @@ __global__ void solve_kernel(SolveArgs a) {
     }
 }
 
-// Canonical [8][K][n] FP64 shape vectors -> tile layouts of the fused step (members 1..K-1):
-//   FP32: element (((j-1) * 2 + h) * kTileNodes + b) * 4 + r, direction k = 1 + 4 h + r
-//   FP64: element (((j-1) * 4 + q) * kTileNodes + b) * 2 + r, direction k = 1 + 2 q + r
+// Canonical [8][K][n] FP64 shape vectors -> tile layouts of the fused step:
+//   FP32 (members j = 1..K-1): element (((j-1) * 2 + h) * kTileNodes + b) * 4 + r, k = 1 + 4 h + r
+//   FP64 (members j = 0..K-1): element ((j * 4 + q) * kTileNodes + b) * 2 + r,     k = 1 + 2 q + r
 __global__ void repack_kernel(const TileDev *__restrict__ tiles, int ntiles, const SegDev *__restrict__ seg,
                               const double *__restrict__ w64c, float *__restrict__ w32t,
                               double *__restrict__ w64t) {
@@ -206,9 +234,9 @@ __global__ void repack_kernel(const TileDev *__restrict__ tiles, int ntiles, con
         const SegDev &sd = seg[tile.seg];
         const int K = tile.K;
         const int64_t il0 = tile.begin - sd.off;
-        const int64_t total = (int64_t)(K - 1) * 8 * B;
-        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-            if (w32t) {
+        if (w32t) {
+            const int64_t total = (int64_t)(K - 1) * 8 * B;
+            for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
                 const int r = (int)(e & 3);
                 const int64_t q4 = e >> 2;
                 const int b = (int)(q4 % B);
@@ -217,14 +245,17 @@ __global__ void repack_kernel(const TileDev *__restrict__ tiles, int ntiles, con
                 double v = b < tile.count ? w64c[sd.w_off + ((int64_t)(k - 1) * K + j) * sd.n + il0 + b] : 0.0;
                 w32t[tile.w_off + e] = (float)v;
             }
-            if (w64t) {
+        }
+        if (w64t) {
+            const int64_t total = (int64_t)K * 8 * B;
+            for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
                 const int r = (int)(e & 1);
                 const int64_t q2 = e >> 1;
                 const int b = (int)(q2 % B);
                 const int64_t jq = q2 / B;
-                const int q = (int)(jq & 3), j = (int)(jq >> 2) + 1, k = 1 + 2 * q + r;
+                const int q = (int)(jq & 3), j = (int)(jq >> 2), k = 1 + 2 * q + r;
                 double v = b < tile.count ? w64c[sd.w_off + ((int64_t)(k - 1) * K + j) * sd.n + il0 + b] : 0.0;
-                w64t[tile.w_off + e] = v;
+                w64t[tile.w64_off + e] = v;
             }
         }
     }
@@ -278,26 +309,29 @@ void free_weights(mlbm_weights *w) {
 
 // Solve all systems of a weights object (device arrays must be in place).  Returns the number
 // of bad systems through nbad_out.
-int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStream_t st,
-                  int warps_per_block, int64_t *nbad_out) {
-    int nmax = 0;
-    for (auto &s : w->seg) nmax = std::max(nmax, s.K + s.m);
+struct SolveShape {
+    int slot;    // doubles per warp
+    int nmax;
+};
+
+static SolveShape solve_shape(const mlbm_weights *w) {
+    int nmax = 0, kmax = 0;
+    for (auto &s : w->seg) {
+        nmax = std::max(nmax, s.K + s.m);
+        kmax = std::max(kmax, s.K);
+    }
     const int ld = (nmax + 8) | 1;
-    const int slot = nmax * ld + 2 * kMaxK;
-    int maxsm = 0;
-    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
-    if (warps_per_block < 1) warps_per_block = 4;
-    while (warps_per_block > 1 && (size_t)warps_per_block * slot * sizeof(double) > (size_t)maxsm)
-        warps_per_block >>= 1;
-    size_t smem = (size_t)warps_per_block * slot * sizeof(double);
-    if (smem > (size_t)maxsm) return fail(MLBM_EINVAL, "collocation system too large for shared memory");
-    int rc = cuda_check(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem),
+    return SolveShape{nmax * ld + 2 * kmax, nmax};
+}
+
+// Launch the solver over nodes [0, count) with `wpb` warps (one system each) per CTA.
+static int launch_solve(mlbm_weights *w, const double *d_x, const double *d_y, unsigned long long *d_bad,
+                        int64_t count, int wpb, cudaStream_t st) {
+    const SolveShape sh = solve_shape(w);
+    const size_t smem = (size_t)wpb * sh.slot * sizeof(double);
+    int rc = cuda_check(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                         "cudaFuncSetAttribute(solve)");
     if (rc) return rc;
-    unsigned long long *d_bad = nullptr;
-    if ((rc = dev_alloc(&d_bad, 1, "bad counter"))) return rc;
-    cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st);
     SolveArgs a;
     a.seg = w->d_seg;
     a.x = d_x;
@@ -306,18 +340,93 @@ int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStr
     a.node_seg = w->d_node_seg;
     a.w64 = w->d_w64;
     a.nbad = d_bad;
-    a.N = w->N;
-    a.slot = slot;
+    a.N = count;
+    a.slot = sh.slot;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, 32 * warps_per_block, smem);
-    int64_t need = (w->N + warps_per_block - 1) / warps_per_block;
-    int64_t grid = std::min<int64_t>(need, (int64_t)std::max(1, per_sm) * w->num_sms);
-    solve_kernel<<<(unsigned)grid, 32 * warps_per_block, smem, st>>>(a);
-    rc = cuda_check(cudaGetLastError(), "solve_kernel launch");
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, 32 * wpb, smem);
+    const int64_t need = (count + wpb - 1) / wpb;
+    const int64_t grid = std::min<int64_t>(need, (int64_t)std::max(1, per_sm) * w->num_sms);
+    solve_kernel<<<(unsigned)grid, 32 * wpb, smem, st>>>(a);
+    return cuda_check(cudaGetLastError(), "solve_kernel launch");
+}
+
+// Autotuner of the batched solver's CTA shape: for launches of at least `kTuneMin` systems,
+// each warps-per-CTA candidate that fits in shared memory is timed (CUDA events) on the first
+// systems of the batch and the fastest is kept, cached per largest system size.
+static int tune_warps(mlbm_weights *w, const double *d_x, const double *d_y, unsigned long long *d_bad,
+                      cudaStream_t st, int *best_wpb) {
+    static std::map<int, int> cache;
+    static std::mutex cache_mu;
+    const SolveShape sh = solve_shape(w);
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
+    auto fits = [&](int wpb) { return (size_t)wpb * sh.slot * sizeof(double) <= (size_t)maxsm; };
+    *best_wpb = 0;
+    for (int wpb = 4; wpb >= 1; wpb >>= 1)
+        if (fits(wpb)) {
+            *best_wpb = wpb;
+            break;
+        }
+    if (!*best_wpb) return fail(MLBM_EINVAL, "collocation system too large for shared memory");
+    constexpr int64_t kTuneMin = 200000;
+    if (w->N < kTuneMin) return MLBM_OK;
+    {
+        std::lock_guard<std::mutex> lk(cache_mu);
+        auto it = cache.find(sh.nmax);
+        if (it != cache.end() && fits(it->second)) {
+            *best_wpb = it->second;
+            return MLBM_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    const int64_t sample = std::min<int64_t>(w->N, (int64_t)w->num_sms * 96);
+    for (int wpb : {1, 2, 4, 8, 12, 16}) {
+        if (!fits(wpb)) continue;
+        int rc = launch_solve(w, d_x, d_y, d_bad, sample, wpb, st);  // warm the configuration
+        if (!rc) {
+            cudaEventRecord(e0, st);
+            rc = launch_solve(w, d_x, d_y, d_bad, sample, wpb, st);
+            cudaEventRecord(e1, st);
+        }
+        if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "solver tuning");
+        if (rc) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            *best_wpb = wpb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(cache_mu);
+    cache[sh.nmax] = *best_wpb;
+    return MLBM_OK;
+}
+
+// Solve all systems of a weights object (device arrays in place).  warps_per_block <= 0 asks
+// the autotuner.  The number of bad systems is returned through nbad_out.
+int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStream_t st,
+                  int warps_per_block, int64_t *nbad_out) {
+    unsigned long long *d_bad = nullptr;
+    int rc = dev_alloc(&d_bad, 1, "bad counter");
+    if (rc) return rc;
+    int wpb = warps_per_block;
+    if (wpb <= 0) rc = tune_warps(w, d_x, d_y, d_bad, st, &wpb);
+    if (!rc) rc = cuda_check(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st), "memset");
+    if (!rc) rc = launch_solve(w, d_x, d_y, d_bad, w->N, wpb, st);
     unsigned long long nbad = 0;
     if (!rc) rc = cuda_check(cudaMemcpyAsync(&nbad, d_bad, sizeof(nbad), cudaMemcpyDeviceToHost, st), "copy");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "solve_kernel");
     cudaFree(d_bad);
+    w->solve_wpb = wpb;
     if (nbad_out) *nbad_out = (int64_t)nbad;
     return rc;
 }
@@ -333,7 +442,7 @@ int repack_weights(mlbm_weights *w, cudaStream_t st) {
 }
 
 int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
-                std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total);
+                std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total, int64_t &wt64_total);
 
 }  // namespace mlbm
 
@@ -416,7 +525,7 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     std::vector<TileDev> tiles;
     std::vector<int32_t> halo;
     std::vector<uint32_t> lidx;
-    if (!rc) rc = build_tiles(c, tiles, halo, lidx, w->umax, w->wt_total);
+    if (!rc) rc = build_tiles(c, tiles, halo, lidx, w->umax, w->wt_total, w->wt64_total);
     if (rc) {
         free_weights(w);
         return rc;
@@ -444,11 +553,11 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     if (!rc) rc = upload(&w->d_halo, halo.data(), halo.size(), "halo lists");
     if (!rc) rc = upload(&w->d_lidx, lidx.data(), lidx.size(), "stencil slots");
     if (!rc) rc = dev_alloc(&w->d_w64, (size_t)w->w_total, "W64");
-    if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64t, (size_t)w->wt_total, "W64 tiles");
+    if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64t, (size_t)w->wt64_total, "W64 tiles");
     if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32t, (size_t)w->wt_total, "W32 tiles");
     if (!rc) rc = dev_alloc(&w->d_params, (size_t)4 * c->nseg, "params");
     int64_t nbad = 0;
-    if (!rc) rc = solve_weights(w, d_x, d_y, st, 4, &nbad);
+    if (!rc) rc = solve_weights(w, d_x, d_y, st, 0, &nbad);
     if (!rc) rc = repack_weights(w, st);
     cudaFree(d_x);
     cudaFree(d_y);
