@@ -64,9 +64,10 @@ __device__ __forceinline__ void collide(T (&s)[9], T rho_ref, T inv_tau, T gx, T
 }
 
 // FP32 collision with exact conservation by construction.  With rounded lattice weights
-// (fl(1/9), fl(1/36)) the equilibrium's mass and momentum differ from those of fhat by a fixed
-// relative amount (3 (2 omega_1 + 4 omega_5) = 1 + 2.2e-8 in FP32), which would rescale the
-// momentum of every node identically at every step.  The non-equilibrium part n = fhat - f^eq
+// (fl(1/9), fl(1/36)) the equilibrium's mass and momentum differ from those of fhat by fixed
+// relative amounts (3 (2 fl(1/9) + 4 fl(1/36)) = 1 + 7.45e-9 exactly, plus the rounding of the
+// other constants), which would rescale the momentum of every node in the same direction at
+// every step (a drift of order 1e-8 per step).  The non-equilibrium part n = fhat - f^eq
 // is therefore projected onto zero mass and momentum with exact operations (its mass is taken
 // from n_0, half of its x / y momentum from each of n_1, n_3 / n_2, n_4) before relaxing.
 __device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, float inv_tau, float gx, float gy,
