@@ -228,6 +228,35 @@ int mlbm_norms(const mlbm_weights *w, const double *a, const double *b, const do
                const double *d, int64_t n, double *out, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * mlbm_norms_noalloc -- the sums of mlbm_norms computed without allocating any memory.  The
+ * paper has no counterpart; this is a library facility.
+ *
+ * Some callers cannot call cudaMalloc: code that runs while a memory pool owns the device
+ * (a framework's caching allocator that has reserved the free memory, where an extra
+ * cudaMalloc fails or fragments the pool), latency-critical loops that cannot afford the
+ * implicit device synchronisation of cudaMalloc / cudaFree, and monitoring code that must not
+ * change the process's memory footprint.  mlbm_norms needs a weights object whose scratch it
+ * allocates on first use; this variant needs no weights object and calls no allocating
+ * routine (no cudaMalloc, cudaFree or library allocator).  Its scratch is a fixed array of
+ * 4096 x 3 doubles (96 KiB) in the library's own device memory, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ *   a, b, c, d  device, n float64 each (c and d may both be NULL: single component)
+ *   n           0 <= n <= 16,777,216 (4096 blocks of 4096 elements); larger n returns
+ *               MLBM_EINVAL with a message naming the limit, and nothing is launched
+ *   out         device, 3 float64: the same three sums as mlbm_norms (summed in a different
+ *               block order, so equal to rounding, not bitwise)
+ * The call is stream-ordered and asynchronous (it does not synchronise).  The first call on
+ * each device looks up the scratch array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture on the device.  All calls
+ * share the one array and it keeps the last call's partial sums: calls that overlap on the
+ * GPU (different streams or host threads without ordering) race and give wrong results.
+ * Errors: MLBM_EINVAL, MLBM_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const double *d,
+                       int64_t n, double *out, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Adjoint (discrete reverse mode of the step above).  With s^{n+1} = Step(s^n; tau, g):
  *
  * mlbm_adjoint_step: given lam_next = dL/ds^{n+1}, writes lam_prev = dL/ds^n (the transpose

@@ -26,7 +26,7 @@ from . import build as _build
 __all__ = [
     "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
-    "moments", "norms", "adjoint_step", "moments_adjoint", "init_adjoint",
+    "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -86,6 +86,7 @@ def lib():
             L.mlbm_run.argtypes = [_vp, _vp, _c_int, _vp, _vp, _c_i64, _vp]
             L.mlbm_moments.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_norms.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
+            L.mlbm_norms_noalloc.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
             L.mlbm_adjoint_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_moments_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_init_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -324,6 +325,23 @@ def norms(w: Weights, a, b, c=None, d=None, stream=None):
                             _dev_ptr(c, torch.float64, n, "c") if c is not None else None,
                             _dev_ptr(d, torch.float64, n, "d") if d is not None else None,
                             n, out.ctypes.data, _stream(stream)))
+    return out
+
+
+def norms_noalloc(a, b, c=None, d=None, out=None, stream=None):
+    """The sums of ``norms`` into the device tensor ``out`` (3 float64) without any memory
+    allocation in the library (for callers that cannot allocate device memory; n is limited to
+    16,777,216 and overlapping calls race, see mlbm_norms_noalloc in include/mlbm.h)."""
+    import torch
+
+    n = a.numel()
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device=a.device)
+    _check(lib().mlbm_norms_noalloc(_dev_ptr(a, torch.float64, n, "a"),
+                                    _dev_ptr(b, torch.float64, n, "b"),
+                                    _dev_ptr(c, torch.float64, n, "c") if c is not None else None,
+                                    _dev_ptr(d, torch.float64, n, "d") if d is not None else None,
+                                    n, _dev_ptr(out, torch.float64, 3, "out"), _stream(stream)))
     return out
 
 

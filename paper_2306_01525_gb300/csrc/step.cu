@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -423,6 +424,48 @@ int launch_step(const mlbm_weights *w, int dtype, const void *fin, void *fout, v
                              : launch_step_t<double>(w, fin, fout, mom, st);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the norms reduction.
+//
+// The per-block partial sums live in a fixed array in the library's own device memory instead
+// of a buffer from cudaMalloc, so the call allocates nothing.  Each block reduces at most
+// kNoallocChunk elements, so the array bounds n.  Host code cannot use the array's name as a
+// device address; the address is looked up once per device with cudaGetSymbolAddress.
+constexpr int kNoallocChunk = kNormThreads * 16;                             // elements per block
+constexpr int kNoallocMaxBlocks = 4096;                                      // 96 KiB of partials
+constexpr int64_t kNoallocMaxN = (int64_t)kNoallocMaxBlocks * kNoallocChunk;  // 16,777,216
+
+static __device__ __align__(256) double g_norms_scratch[3 * kNoallocMaxBlocks];
+
+namespace {
+constexpr int kMaxDevicesNoalloc = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[kMaxDevicesNoalloc] = {nullptr};
+
+// Device address of g_norms_scratch on the current device (looked up on first use).
+int noalloc_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MLBM_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    }
+    if (dev < 0 || dev >= kMaxDevicesNoalloc) return fail(MLBM_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_norms_scratch);
+        if (e != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return fail(MLBM_ECUDA, std::string("cudaGetSymbolAddress(norms scratch): ") + cudaGetErrorString(e));
+        }
+        g_noalloc_ptr[dev] = (double *)ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return MLBM_OK;
+}
+}  // namespace
+
 }  // namespace mlbm
 
 using namespace mlbm;
@@ -548,6 +591,25 @@ int mlbm_norms(const mlbm_weights *w, const double *a, const double *b, const do
                          "norms copy");
     if (rc) return rc;
     return cuda_check_step(cudaStreamSynchronize(st), "norms");
+}
+
+int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const double *d, int64_t n,
+                       double *out, void *stream) {
+    set_error("");
+    if (!a || !b || !out || n < 0) return fail(MLBM_EINVAL, "bad argument");
+    if ((c == nullptr) != (d == nullptr)) return fail(MLBM_EINVAL, "c and d must both be given or both NULL");
+    if (n > kNoallocMaxN)
+        return fail(MLBM_EINVAL, "n = " + std::to_string(n) + " exceeds the limit of mlbm_norms_noalloc (" +
+                                     std::to_string(kNoallocMaxN) + " elements); use mlbm_norms");
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = (int)std::max<int64_t>(1, (n + kNoallocChunk - 1) / kNoallocChunk);
+    // every partial slot read by the second pass is written by the first, so nothing to clear
+    norms_pass1<<<blocks, kNormThreads, 0, st>>>(a, b, c, d, n, scratch);
+    norms_pass2<<<1, kNormThreads, 0, st>>>(scratch, blocks, out);
+    return cuda_check_step(cudaGetLastError(), "norms (no allocation) launch");
 }
 
 }  // extern "C"
