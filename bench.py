@@ -194,6 +194,176 @@ def _config(workload, world):
     }
 
 
+def annulus_profile(r, g, nu, r1, r2):
+    """Analytic azimuthal speed of force-driven flow between two circles, eq. (bch_solution):
+    u(r) = -G (r^2 - alpha r + beta / r), G = g / (3 nu), alpha = (r1^2 + r1 r2 + r2^2) / (r1 + r2),
+    beta = r1^2 r2^2 / (r1 + r2); used only to report the error of a run."""
+    G = g / (3.0 * nu)
+    alpha = (r1 * r1 + r1 * r2 + r2 * r2) / (r1 + r2)
+    beta = r1 * r1 * r2 * r2 / (r1 + r2)
+    return -G * (r * r - alpha * r + beta / r)
+
+
+def lattice_nu(tau):
+    """Lattice viscosity c_s^2 (tau - 1/2) (Sec. 2.1, as fixed by the Sec. 3 parameters)."""
+    return (tau - 0.5) / 3.0
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Maximum of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_batched(steps: int, warmup: int = 5):
+    """The batched convergence sweep: 64 independent Taylor-Green runs (uneven N, N_L, degree,
+    dx_ml) as segments of one cloud: one uneven FP64 solve launch, then FP32 steps of all runs
+    in one persistent launch each, graph-captured."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    runs = mi.sweep_runs()
+    parts, segs, params, us, vs = [], [], [], [], []
+    for r in runs:
+        xy = mi.jittered_lattice(r["n_side"], 0.3, seed=r["seed"])
+        parts.append(xy)
+        segs.append(dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=r["K"], degree=r["degree"],
+                         dx_ml=r["ratio"] / r["n_side"]))
+        params.append((r["tau"], 0.0, 1.0))
+        _, u, v = mi.tgv_initial(xy, r["u0"])
+        us.append(u)
+        vs.append(v)
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    t0 = time.perf_counter()
+    cloud = mlbm.build_cloud(xy, segs, offs)
+    t_cloud = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w = mlbm.build_weights(cloud)
+    torch.cuda.synchronize()
+    t_weights = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = w.n
+    td = lambda a: torch.as_tensor(a, dtype=torch.float64, device=dev)
+    a = torch.empty(9 * N, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F32, td(np.ones(N)), td(np.concatenate(us)), td(np.concatenate(vs)), a)
+    a = mlbm.run(w, params, mlbm.F32, a, b, warmup)
+    b = b if a is not b else torch.empty_like(a)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    mlbm.run(w, params, mlbm.F32, a, b, steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    byts = sum(int(offs[i + 1] - offs[i]) * step_bytes_per_node(r["K"], 4) for i, r in enumerate(runs))
+    peak, _ = _peaks()
+    achieved = byts / (ms / steps * 1e-3) / 1e9
+    return {"workload": "tgv_sweep_64runs", "runs": len(runs), "nodes": N,
+            "stencils": sorted({r["K"] for r in runs}), "degrees": sorted({r["degree"] for r in runs}),
+            "value": N * steps / (ms * 1e-3) / 1e9, "unit": UNIT, "steps": steps,
+            "ms_per_step": ms / steps, "achieved_gbs": achieved, "frac_of_hbm": achieved / peak,
+            "launches_per_step": 1, "setup_s": {"cloud_host": t_cloud, "weights_gpu": t_weights}}
+
+
+def bench_annulus(max_steps: int = 500000, chunk: int = 2000):
+    """Annular channel, about 20k scattered nodes, N_L = 20, P_3, tau = 0.7, g = 1e-6, dx_ml =
+    1/320, FP64, run until the relative velocity residual per step falls below 1e-10 or
+    max_steps; L2 error of the speed vs the analytic profile."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    dx, tau, g = 1.0 / 320, 0.7, 1e-6
+    xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[20000], seed=2)
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=20, degree=3, dx_ml=dx))
+    w = mlbm.build_weights(cloud)
+    n = w.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    td = lambda x: torch.as_tensor(x, dtype=torch.float64, device=dev)
+    params = [(tau, g, 1.0)]
+    a = torch.empty(9 * n, dtype=torch.float64, device=dev)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F64, td(np.ones(n)), td(np.zeros(n)), td(np.zeros(n)), a)
+    prev, done, res = None, 0, float("inf")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while done < max_steps:
+        a = mlbm.run(w, params, mlbm.F64, a, b, chunk)
+        b = b if a is not b else torch.empty_like(a)
+        done += chunk
+        _, u, v = mlbm.moments(w, params, mlbm.F64, a)
+        if prev is not None:
+            s = mlbm.norms(w, u, prev[0], v, prev[1])
+            res = float(np.sqrt(s[0] / s[2]) / chunk)
+            if res < 1e-10:
+                break
+        prev = (u.clone(), v.clone())
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    r = np.hypot(xy[0], xy[1])
+    want = np.abs(annulus_profile(r / dx, g, lattice_nu(tau), 0.5 / dx, 1.0 / dx))
+    uu, vv = u.cpu().numpy(), v.cpu().numpy()
+    err = float(np.sqrt(np.sum((np.hypot(uu, vv) - want) ** 2) / np.sum(want ** 2)))
+    return {"workload": "annulus_20k_k20_d3", "nodes": n, "steps": done, "residual_per_step": res,
+            "l2_speed_vs_analytic": err, "value": n * done / el / 1e9, "unit": UNIT,
+            "ms_per_step": el / done * 1e3, "dtype": "f64",
+            "note": "wall time of the whole run incl. residual checks every %d steps" % chunk}
+
+
+def bench_adjoint(steps: int = 2000):
+    """Adjoint of the annulus with about 250k scattered nodes, N_L = 24, P_3, FP32 steps with
+    sqrt(T) checkpointing: gradient of the velocity-profile mismatch w.r.t. tau, g and the
+    initial fields; time of forward plus backward."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+    from paper_2306_01525_gb300.autograd import rollout
+
+    dx, tau, g = 1.0 / 320, 0.7, 1e-5
+    xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[250000], seed=5)
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=24, degree=3, dx_ml=dx))
+    w = mlbm.build_weights(cloud)
+    n = w.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    r = np.hypot(xy[0], xy[1])
+    target = torch.as_tensor(np.abs(annulus_profile(r / dx, g, lattice_nu(tau), 0.5 / dx, 1.0 / dx)),
+                             device=dev)
+    tt = torch.tensor(tau, dtype=torch.float64, device=dev, requires_grad=True)
+    gt = torch.tensor(g, dtype=torch.float64, device=dev, requires_grad=True)
+    r0 = torch.ones(n, dtype=torch.float64, device=dev, requires_grad=True)
+    a0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
+    b0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    t0 = time.perf_counter()
+    rho, u, v = rollout(w, tt, gt, r0, a0, b0, steps, dtype=mlbm.F32)
+    loss = ((torch.sqrt(u * u + v * v + 1e-30) - target) ** 2).sum()
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    loss.backward()
+    torch.cuda.synchronize()
+    t_all = time.perf_counter() - t0
+    return {"workload": "annulus_250k_k24_d3_adjoint", "nodes": n, "steps": steps, "dtype": "f32",
+            "checkpoint_every": int(np.ceil(np.sqrt(steps))), "forward_s": t_fwd,
+            "forward_backward_s": t_all, "loss": float(loss),
+            "dloss_dtau": float(tt.grad), "dloss_dg": float(gt.grad),
+            "dloss_du0_norm": float(a0.grad.norm()),
+            "peak_torch_mem_gb": torch.cuda.max_memory_allocated() / 1e9}
+
+
 def _dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -281,11 +451,8 @@ def run_mlbm(args):
         e1.record(stream)
         torch.cuda.synchronize()
         clk = clocks.stop() if clocks else None
-        ms = e0.elapsed_time(e1)
+        ms = reduce_max(e0.elapsed_time(e1), dist, dev)
         if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
             dist.barrier()
         return ms, clk
 
@@ -328,11 +495,7 @@ def run_mlbm(args):
         h_out.copy_(b, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / e2e_steps
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = reduce_max(e0.elapsed_time(e1) / e2e_steps, dist, dev)
     gnups_e2e = N * world / (ms_e2e * 1e-3) / 1e9
     del h_in, h_out, a, b
 
@@ -348,6 +511,15 @@ def run_mlbm(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_gnups(args.cpu_seconds)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        del w
+        torch.cuda.empty_cache()
+        extras["batched"] = bench_batched(1000)
+        torch.cuda.empty_cache()
+        extras["annulus"] = bench_annulus()
+        torch.cuda.empty_cache()
+        extras["adjoint"] = bench_adjoint(2000)
     line = {
         "metric": METRIC, "value": gnups32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step32, "higher_is_better": True,
@@ -367,6 +539,7 @@ def run_mlbm(args):
         "fp32_vs_fp64_rel_l2_u": err, "error_steps": args.err_steps,
         "setup_s": {"cloud_host": t_cloud, "weights_gpu": t_weights},
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -377,13 +550,15 @@ def run_mlbm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mlbm", choices=["mlbm", "reference"])
     ap.add_argument("--workload", default="tgv_large", choices=sorted(WORKLOADS))
     ap.add_argument("--err-steps", type=int, default=10000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-sweep, annulus and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

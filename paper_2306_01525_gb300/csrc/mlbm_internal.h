@@ -56,8 +56,10 @@ struct SegDev {
     double lx, ly, dx_ml, pad;
 };
 
-// Nodes per tile of the fused step: one CTA pass over a contiguous Morton run.
+// Nodes per tile of the fused step (one CTA pass over a contiguous Morton run): large tiles
+// for clouds with enough tiles to fill the GPU, small tiles otherwise.
 constexpr int kTileNodes = 512;
+constexpr int kTileNodesSmall = 128;
 
 // A tile: a contiguous run of stored nodes of one segment processed by one CTA pass.
 // Its halo (the tile's own nodes first, then every other node its stencils read, sorted) is

@@ -105,20 +105,20 @@ __device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const d
     d[1] = c.y + a.y;
 }
 
-// One fused time step over all tiles (persistent CTAs, one node per thread, kTileNodes threads):
+// One fused time step over all tiles (persistent CTAs, one node per thread, B threads per CTA
+// and B nodes per tile):
 //   1. stage f^post_k (k = 1..8) of the tile's halo in shared memory as [slot][8];
 //   2. FP32: fhat_k(i) = f_k(i) + sum_{j>=1} W_k[j](i) (f_k(s_j(i)) - f_k(i)) -- the shape vector
 //      sums to one (constant reproduction), so the centre weight is implied and never loaded,
 //      and rounding of the FP32 weights only touches the small differences;
 //      FP64: fhat_k(i) = sum_{j>=0} W_k[j](i) f_k(s_j(i)) as written in eq. (shape_vector);
 //   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
-template <typename T>
-__global__ void __launch_bounds__(kTileNodes, (sizeof(T) == 4 ? 2 : 1)) step_kernel(StepArgs<T> a) {
+template <typename T, int B>
+__global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)) step_kernel(StepArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;  // vectors per 8 moving populations
-    constexpr int B = kTileNodes;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     const int64_t N = a.N;
@@ -395,14 +395,19 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.N = w->N;
     a.ntiles = w->ntiles;
     const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
-    step_kernel<T><<<grid, kTileNodes, step_smem<T>(w), st>>>(a);
+    if (w->tile_nodes == kTileNodes)
+        step_kernel<T, kTileNodes><<<grid, kTileNodes, step_smem<T>(w), st>>>(a);
+    else
+        step_kernel<T, kTileNodesSmall><<<grid, kTileNodesSmall, step_smem<T>(w), st>>>(a);
     return cuda_check_step(cudaGetLastError(), "step_kernel launch");
 }
 
 // Persistent grids of the step kernels: CTAs resident per SM x SMs, capped by the tile count.
 // A precision whose halo does not fit in shared memory gets grid 0 and is refused by the step.
 int prepare_step_grids(mlbm_weights *w) {
-    const void *fns[2] = {(const void *)step_kernel<float>, (const void *)step_kernel<double>};
+    const bool big = w->tile_nodes == kTileNodes;
+    const void *fns[2] = {big ? (const void *)step_kernel<float, kTileNodes> : (const void *)step_kernel<float, kTileNodesSmall>,
+                          big ? (const void *)step_kernel<double, kTileNodes> : (const void *)step_kernel<double, kTileNodesSmall>};
     const size_t sm[2] = {step_smem<float>(w), step_smem<double>(w)};
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
@@ -413,7 +418,7 @@ int prepare_step_grids(mlbm_weights *w) {
                                  "step shared-memory attribute");
         if (rc) return rc;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], kTileNodes, sm[i]);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], w->tile_nodes, sm[i]);
         w->step_grid[i] = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
     }
     return MLBM_OK;

@@ -1,7 +1,7 @@
-// Tile tables of the fused step: for each run of kTileNodes stored nodes of one segment, the
+// Tile tables of the fused step: for each run of B (kTileNodes or kTileNodesSmall) stored nodes of one segment, the
 // halo of nodes its stencils read (own nodes first, then the others sorted), and the 16-bit halo
 // slot of every stencil member j = 1..K-1 (member 0 is the node itself, Sec. 2.2), packed two per
-// 32-bit word as [ceil((K-1)/2)][kTileNodes].
+// 32-bit word as [ceil((K-1)/2)][B].
 #include <algorithm>
 #include <string>
 #include <thread>
@@ -11,24 +11,24 @@
 
 namespace mlbm {
 
-int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
+int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
                 std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total, int64_t &wt64_total) {
     tiles.clear();
     int64_t w_off = 0, w64_off = 0, l_off = 0;
     for (int s = 0; s < c->nseg; ++s) {
         const SegmentHost &h = c->seg[s];
-        for (int64_t b = 0; b < h.n; b += kTileNodes) {
+        for (int64_t b = 0; b < h.n; b += B) {
             TileDev t{};
             t.begin = h.off + b;
-            t.count = (int32_t)std::min<int64_t>(kTileNodes, h.n - b);
+            t.count = (int32_t)std::min<int64_t>(B, h.n - b);
             t.seg = s;
             t.K = h.K;
             t.w_off = w_off;
             t.w64_off = w64_off;
             t.l_off = l_off;
-            w_off += (int64_t)(h.K - 1) * 8 * kTileNodes;
-            w64_off += (int64_t)h.K * 8 * kTileNodes;
-            l_off += (int64_t)((h.K - 1 + 1) / 2) * kTileNodes;
+            w_off += (int64_t)(h.K - 1) * 8 * B;
+            w64_off += (int64_t)h.K * 8 * B;
+            l_off += (int64_t)((h.K - 1 + 1) / 2) * B;
             tiles.push_back(t);
         }
     }
@@ -71,7 +71,7 @@ int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<in
                 const int jp = (j - 1) >> 1, hi = (j - 1) & 1;
                 for (int b = 0; b < T.count; ++b) {
                     uint32_t sl = slot(idx[(int64_t)j * h.n + il0 + b]);
-                    lidx[T.l_off + (int64_t)jp * kTileNodes + b] |= hi ? (sl << 16) : sl;
+                    lidx[T.l_off + (int64_t)jp * B + b] |= hi ? (sl << 16) : sl;
                 }
             }
         }

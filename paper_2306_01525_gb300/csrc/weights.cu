@@ -47,6 +47,22 @@ __device__ __forceinline__ double d_mono(int l, double x, double y) {
     return d_ipow(x, c_mono_px[l]) * d_ipow(y, c_mono_py[l]);
 }
 
+constexpr int kMaxMono = (kMaxDegree + 1) * (kMaxDegree + 2) / 2;
+
+// All monomials x^a y^b, a + b <= deg, by total degree then decreasing power of x, from
+// running powers (one multiplication each).
+__device__ __forceinline__ void d_monomials(int deg, double x, double y, double *out) {
+    double px[kMaxDegree + 1], py[kMaxDegree + 1];
+    px[0] = py[0] = 1.0;
+    for (int i = 1; i <= deg; ++i) {
+        px[i] = px[i - 1] * x;
+        py[i] = py[i - 1] * y;
+    }
+    int c = 0;
+    for (int t = 0; t <= deg; ++t)
+        for (int b = 0; b <= t; ++b) out[c++] = px[t - b] * py[b];
+}
+
 __device__ __forceinline__ double d_phi(double dx, double dy) {
     double r = sqrt(dx * dx + dy * dy);
     return r * r * r;
@@ -77,6 +93,7 @@ __global__ void solve_kernel(SolveArgs a) {
         const int K = sd.K, m = sd.m, n = K + m, ld = ld_of(n), nc = n + 8;
         double *tx = A + n * ld;
         double *ty = tx + K;
+        double *M = ty + K;  // monomials of the scaled stencil points, [K][m]
         const int64_t il = node - sd.off;
         const double xi = a.x[node], yi = a.y[node];
         const double lx = sd.geometry == MLBM_GEOM_PERIODIC ? sd.lx : 0.0;
@@ -92,32 +109,42 @@ __global__ void solve_kernel(SolveArgs a) {
         }
         for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
         const double s = rmax > 0.0 ? rmax : 1.0;
+        const double is = 1.0 / s;
         for (int j = lane; j < K; j += 32) {
-            tx[j] /= s;
-            ty[j] /= s;
+            const double x = tx[j] * is, y = ty[j] * is;
+            tx[j] = x;
+            ty[j] = y;
+            d_monomials(sd.deg, x, y, M + j * m);
         }
         __syncwarp();
         // augmented matrix [Phi_L | phi_L(q_1) ... phi_L(q_8)], q_k = -e_k dx_ml / s
-        const double dq = sd.dx_ml / s;
+        const double dq = sd.dx_ml * is;
         double amax = 0.0;
-        for (int e = lane; e < n * nc; e += 32) {
-            int r = e / nc, c = e - r * nc;
-            double v;
-            if (c >= n) {
-                int k = c - n + 1;
-                double qx = -kEx[k] * dq, qy = -kEy[k] * dq;
-                v = (r < K) ? d_phi(qx - tx[r], qy - ty[r]) : d_mono(r - K, qx, qy);
-            } else if (r < K && c < K) {
-                v = d_phi(tx[r] - tx[c], ty[r] - ty[c]);
-            } else if (r < K) {
-                v = d_mono(c - K, tx[r], ty[r]);
-            } else if (c < K) {
-                v = d_mono(r - K, tx[c], ty[c]);
+        // R block (symmetric: each pair evaluated once), P and P^T blocks, zero block
+        for (int e = lane; e < n * n; e += 32) {
+            const int r = e / n, c = e - r * n;
+            if (r < K && c < K) {
+                if (r > c) continue;
+                const double v = d_phi(tx[r] - tx[c], ty[r] - ty[c]);
+                A[r * ld + c] = v;
+                A[c * ld + r] = v;
+                amax = fmax(amax, v);
             } else {
-                v = 0.0;
+                const double v = (r < K) ? M[r * m + (c - K)] : ((c < K) ? M[c * m + (r - K)] : 0.0);
+                A[r * ld + c] = v;
+                amax = fmax(amax, fabs(v));
             }
-            if (c < n) amax = fmax(amax, fabs(v));
-            A[r * ld + c] = v;
+        }
+        // right-hand sides: phi(|q_k - x_j|) and the monomials at q_k
+        for (int e = lane; e < 8 * K; e += 32) {
+            const int q = e / K, r = e - q * K, k = q + 1;
+            A[r * ld + n + q] = d_phi(-kEx[k] * dq - tx[r], -kEy[k] * dq - ty[r]);
+        }
+        if (lane < 8) {
+            const int k = lane + 1;
+            double mq[kMaxMono];
+            d_monomials(sd.deg, -kEx[k] * dq, -kEy[k] * dq, mq);
+            for (int l = 0; l < m; ++l) A[(K + l) * ld + n + lane] = mq[l];
         }
         for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         __syncwarp();
@@ -205,7 +232,7 @@ __global__ void solve_kernel(SolveArgs a) {
                 int q = t / m, l = t - q * m;
                 int k = q + 1;
                 double acc = 0.0;
-                for (int j = 0; j < K; ++j) acc = fma(A[j * ld + n + q], d_mono(l, tx[j], ty[j]), acc);
+                for (int j = 0; j < K; ++j) acc = fma(A[j * ld + n + q], M[j * m + l], acc);
                 err = fmax(err, fabs(acc - d_mono(l, -kEx[k] * dq, -kEy[k] * dq)));
             }
             for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
@@ -223,12 +250,12 @@ __global__ void solve_kernel(SolveArgs a) {
 }
 
 // Canonical [8][K][n] FP64 shape vectors -> tile layouts of the fused step:
-//   FP32 (members j = 1..K-1): element (((j-1) * 2 + h) * kTileNodes + b) * 4 + r, k = 1 + 4 h + r
-//   FP64 (members j = 0..K-1): element ((j * 4 + q) * kTileNodes + b) * 2 + r,     k = 1 + 2 q + r
+//   FP32 (members j = 1..K-1): element (((j-1) * 2 + h) * B + b) * 4 + r, k = 1 + 4 h + r
+//   FP64 (members j = 0..K-1): element ((j * 4 + q) * B + b) * 2 + r,     k = 1 + 2 q + r
+// with B the tile size of the weights object.
 __global__ void repack_kernel(const TileDev *__restrict__ tiles, int ntiles, const SegDev *__restrict__ seg,
                               const double *__restrict__ w64c, float *__restrict__ w32t,
-                              double *__restrict__ w64t) {
-    constexpr int B = kTileNodes;
+                              double *__restrict__ w64t, int B) {
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileDev tile = tiles[t];
         const SegDev &sd = seg[tile.seg];
@@ -320,8 +347,10 @@ static SolveShape solve_shape(const mlbm_weights *w) {
         nmax = std::max(nmax, s.K + s.m);
         kmax = std::max(kmax, s.K);
     }
+    int km = 0;
+    for (auto &s : w->seg) km = std::max(km, s.K * s.m);
     const int ld = (nmax + 8) | 1;
-    return SolveShape{nmax * ld + 2 * kmax, nmax};
+    return SolveShape{nmax * ld + 2 * kmax + km, nmax};
 }
 
 // Launch the solver over nodes [0, count) with `wpb` warps (one system each) per CTA.
@@ -435,13 +464,14 @@ int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStr
 int repack_weights(mlbm_weights *w, cudaStream_t st) {
     if (!w->d_w32t && !w->d_w64t) return MLBM_OK;
     int grid = std::max(1, std::min(w->ntiles, 8 * w->num_sms));
-    repack_kernel<<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_seg, w->d_w64, w->d_w32t, w->d_w64t);
+    repack_kernel<<<grid, 256, 0, st>>>(w->d_tiles, w->ntiles, w->d_seg, w->d_w64, w->d_w32t, w->d_w64t,
+                                        w->tile_nodes);
     int rc = cuda_check(cudaGetLastError(), "repack launch");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "repack");
     return rc;
 }
 
-int build_tiles(const mlbm_cloud *c, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
+int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::vector<int32_t> &halo,
                 std::vector<uint32_t> &lidx, int &umax, int64_t &wt_total, int64_t &wt64_total);
 
 }  // namespace mlbm
@@ -502,7 +532,12 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     w->perm = c->perm;
     w->idx_total = c->idx_total;
     w->w_total = c->w_total;
-    w->tile_nodes = kTileNodes;
+    // large tiles when the cloud has at least four per SM, small ones otherwise
+    {
+        int64_t big = 0;
+        for (auto &h : c->seg) big += (h.n + kTileNodes - 1) / kTileNodes;
+        w->tile_nodes = big >= 4LL * std::max(1, w->num_sms) ? kTileNodes : kTileNodesSmall;
+    }
     int rc = upload_monomial_tables();
     // segment table
     std::vector<SegDev> sd(c->nseg);
@@ -525,7 +560,7 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     std::vector<TileDev> tiles;
     std::vector<int32_t> halo;
     std::vector<uint32_t> lidx;
-    if (!rc) rc = build_tiles(c, tiles, halo, lidx, w->umax, w->wt_total, w->wt64_total);
+    if (!rc) rc = build_tiles(c, w->tile_nodes, tiles, halo, lidx, w->umax, w->wt_total, w->wt64_total);
     if (rc) {
         free_weights(w);
         return rc;
