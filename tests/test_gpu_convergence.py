@@ -89,9 +89,9 @@ def _annulus_steady(h_key, K, deg, dx, tau=0.7, g=1e-6, max_steps=150000, chunk=
 
 
 def test_annulus_steady_state_follows_analytic_profile_and_converges():
-    """r in [0.5, 1], dx_ml = 1/160 (below the wall node spacing, so only wall nodes have
-    unknown populations), N_L = 20, P_3, tau = 0.7, g = 1e-6: the profile error falls from the
-    1k- to the 20k-node cloud and the flow is azimuthal."""
+    """r in [0.5, 1], dx_ml = 1/160 (smaller than the wall node spacing of both clouds), N_L = 20,
+    P_3, tau = 0.7, g = 1e-6: the profile error falls from the 1k- to the 20k-node cloud and the
+    flow is azimuthal."""
     e_coarse, res_c, steps_c, ur_c = _annulus_steady(1000, 20, 3, 1.0 / 160)
     e_fine, res_f, steps_f, ur_f = _annulus_steady(20000, 20, 3, 1.0 / 160)
     assert e_fine < 0.01, (e_fine, res_f, steps_f)
