@@ -228,6 +228,25 @@ int mlbm_norms(const mlbm_weights *w, const double *a, const double *b, const do
                const double *d, int64_t n, double *out, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Standard lattice LBM (Sec. 2.1, eq. LBM_streaming): nodes on a periodic nx x ny lattice with
+ * spacing dx_ml, streaming as the index shift f_k(x) <- f^post_k(x - e_k), the same BGK
+ * collision, forcing (direction +x) and state conventions as the meshless step.  The paper
+ * compares the meshless method with it; it is also the limit the meshless step reduces to
+ * when the nodes form that lattice.  Node index iy * nx + ix; no weights object is needed.
+ *
+ * mlbm_lattice_init: f_out (device, [9][nx*ny] dtype) = equilibrium at rho, ux, uy (device,
+ *   nx*ny float64 each) plus the forcing term, as mlbm_init.
+ * mlbm_lattice_step: one step f_in -> f_out (must not alias); moments (device, optional,
+ *   [3][nx*ny] dtype) receives rho, u_x, u_y of the streamed populations.
+ * params points to ONE parameter set.  Errors: MLBM_EINVAL (sizes, tau <= 1/2, dtype), MLBM_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+int mlbm_lattice_init(int64_t nx, int64_t ny, const mlbm_params *params, int dtype,
+                      const double *rho, const double *ux, const double *uy, void *f_out,
+                      void *stream);
+int mlbm_lattice_step(int64_t nx, int64_t ny, const mlbm_params *params, int dtype,
+                      const void *f_in, void *f_out, void *moments, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * mlbm_norms_noalloc -- the sums of mlbm_norms computed without allocating any memory.  The
  * paper has no counterpart; this is a library facility.
  *

@@ -27,6 +27,7 @@ __all__ = [
     "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
     "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
+    "lattice_init", "lattice_step",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -87,6 +88,8 @@ def lib():
             L.mlbm_moments.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_norms.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
             L.mlbm_norms_noalloc.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
+            L.mlbm_lattice_init.argtypes = [_c_i64, _c_i64, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
+            L.mlbm_lattice_step.argtypes = [_c_i64, _c_i64, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_adjoint_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_moments_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_init_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
@@ -343,6 +346,31 @@ def norms_noalloc(a, b, c=None, d=None, out=None, stream=None):
                                     _dev_ptr(d, torch.float64, n, "d") if d is not None else None,
                                     n, _dev_ptr(out, torch.float64, 3, "out"), _stream(stream)))
     return out
+
+
+# ----------------------------------------------------------------------------- lattice LBM
+
+def lattice_init(nx: int, ny: int, params, dtype, rho, ux, uy, f_out, stream=None):
+    """Equilibrium initial state of the standard lattice LBM (node index iy * nx + ix)."""
+    import torch
+
+    n = nx * ny
+    _check(lib().mlbm_lattice_init(nx, ny, _params(params, 1), dtype,
+                                   _dev_ptr(rho, torch.float64, n, "rho"),
+                                   _dev_ptr(ux, torch.float64, n, "ux"),
+                                   _dev_ptr(uy, torch.float64, n, "uy"),
+                                   _dev_ptr(f_out, _torch_dtype(dtype), 9 * n, "f_out"),
+                                   _stream(stream)))
+
+
+def lattice_step(nx: int, ny: int, params, dtype, f_in, f_out, moments_out=None, stream=None):
+    """One standard lattice LBM step (index-shift streaming, eq. LBM_streaming)."""
+    n = nx * ny
+    td = _torch_dtype(dtype)
+    _check(lib().mlbm_lattice_step(nx, ny, _params(params, 1), dtype,
+                                   _dev_ptr(f_in, td, 9 * n, "f_in"), _dev_ptr(f_out, td, 9 * n, "f_out"),
+                                   _dev_ptr(moments_out, td, 3 * n, "moments") if moments_out is not None else None,
+                                   _stream(stream)))
 
 
 # ----------------------------------------------------------------------------- adjoint
