@@ -48,6 +48,9 @@ extern "C" {
 #define MLBM_GEOM_PERIODIC 0 /* periodic box [0,lx) x [0,ly), minimum-image distances */
 #define MLBM_GEOM_ANNULUS 1  /* ring r_in <= |x| <= r_out centred at the origin         */
 
+#define MLBM_STENCIL_OWN 0     /* one stencil per node for all directions (default)        */
+#define MLBM_STENCIL_NEAREST 1 /* stencil of the node nearest to each departure point      */
+
 #define MLBM_F32 32 /* FP32 deviation storage, FP32 arithmetic */
 #define MLBM_F64 64 /* FP64 populations, FP64 arithmetic       */
 
@@ -69,6 +72,11 @@ typedef struct {
     double dx_ml;        /* streaming distance dx_ml (Sec. 2.3), physical units; in lattice
                             units it is 1, so c_k = e_k and the departure point of population
                             k at node i is x_i - e_k dx_ml                                     */
+    int stencil_mode;    /* MLBM_STENCIL_OWN: population k of node i is interpolated in node
+                            i's own stencil, shared by all directions; MLBM_STENCIL_NEAREST:
+                            in the stencil of the Eulerian node nearest to its departure point
+                            (Sec. 2.3 and the appendix algorithm), which lets dx_ml exceed the
+                            node spacing                                                       */
 } mlbm_segment_desc;
 
 /* Per-segment step parameters, lattice units. */
@@ -119,6 +127,13 @@ int mlbm_cloud_perm(const mlbm_cloud *cloud, int64_t *perm);
  * idx (host, [N_L][n_seg] int32), idx[j * n_seg + i] = member j of node i's stencil,
  * i in original segment order. */
 int mlbm_cloud_stencil(const mlbm_cloud *cloud, int seg, int32_t *idx);
+
+/* Departure nodes of segment seg: near (host, [8][n_seg] int32), near[(k-1) * n_seg + i] =
+ * the node (original numbering relative to the segment start) whose stencil interpolates
+ * population k of node i, i in original segment order: the node nearest to x_i - e_k dx_ml by
+ * (squared distance, original index) in MLBM_STENCIL_NEAREST mode, i itself in
+ * MLBM_STENCIL_OWN mode. */
+int mlbm_cloud_departure_nodes(const mlbm_cloud *cloud, int seg, int32_t *near);
 
 /* Bounce-back mask of all nodes in original order: mask (host, n uint16), bit k (1..8)
  * set when population k of the node is an unknown wall population. */
@@ -283,7 +298,8 @@ int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const 
  * transpose, then the transpose of the interpolation done as a deterministic pull over the
  * transposed stencil) and adds dL/dtau and dL/dg of this step to grad (device, 2 * nseg
  * float64, [seg][tau, g]).  s_prev is the forward state s^n (device, [9][N] dtype).
- * lam_next and lam_prev: device [9][N] dtype, must not alias.
+ * lam_next and lam_prev: device [9][N] dtype, must not alias.  Segments must use
+ * MLBM_STENCIL_OWN (else MLBM_EINVAL).
  * ------------------------------------------------------------------------------------- */
 int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtype,
                       const void *s_prev, const void *lam_next, void *lam_prev, double *grad,

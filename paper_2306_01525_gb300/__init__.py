@@ -24,7 +24,8 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "KEEP_W32", "KEEP_W64",
+    "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "STENCIL_OWN", "STENCIL_NEAREST",
+    "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
     "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
     "lattice_init", "lattice_step",
@@ -32,6 +33,7 @@ __all__ = [
 
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5
 PERIODIC, ANNULUS = 0, 1
+STENCIL_OWN, STENCIL_NEAREST = 0, 1
 F32, F64 = 32, 64
 KEEP_W32, KEEP_W64 = 1, 2
 
@@ -40,7 +42,8 @@ _c_int, _c_i64, _c_d, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctype
 
 class SegmentDesc(ctypes.Structure):
     _fields_ = [("geometry", _c_int), ("lx", _c_d), ("ly", _c_d), ("r_in", _c_d),
-                ("r_out", _c_d), ("k", _c_int), ("degree", _c_int), ("dx_ml", _c_d)]
+                ("r_out", _c_d), ("k", _c_int), ("degree", _c_int), ("dx_ml", _c_d),
+                ("stencil_mode", _c_int)]
 
 
 class Params(ctypes.Structure):
@@ -76,6 +79,7 @@ def lib():
             L.mlbm_cloud_perm.argtypes = [_vp, _vp]
             L.mlbm_cloud_stencil.argtypes = [_vp, _c_int, _vp]
             L.mlbm_cloud_bounce_mask.argtypes = [_vp, _vp]
+            L.mlbm_cloud_departure_nodes.argtypes = [_vp, _c_int, _vp]
             L.mlbm_build_weights.argtypes = [_vp, _c_int, _vp, ctypes.POINTER(_vp), _vp]
             L.mlbm_weights_free.argtypes = [_vp]
             L.mlbm_weights_free.restype = None
@@ -178,7 +182,7 @@ class Cloud:
             descs[s] = SegmentDesc(int(d.get("geometry", PERIODIC)), float(d.get("lx", 0.0)),
                                    float(d.get("ly", 0.0)), float(d.get("r_in", 0.0)),
                                    float(d.get("r_out", 0.0)), int(d["k"]), int(d["degree"]),
-                                   float(d["dx_ml"]))
+                                   float(d["dx_ml"]), int(d.get("stencil_mode", STENCIL_OWN)))
         h = _vp()
         _check(lib().mlbm_build_cloud(xy.ctypes.data, n, descs, offs.ctypes.data, nseg,
                                       ctypes.byref(h)))
@@ -201,6 +205,14 @@ class Cloud:
         ns = int(self.offsets[seg + 1] - self.offsets[seg])
         out = np.zeros((int(self.segments[seg]["k"]), ns), np.int32)
         _check(lib().mlbm_cloud_stencil(self._h, seg, out.ctypes.data))
+        return out
+
+    def departure_nodes(self, seg=0):
+        """[8][n_seg] int32: the node whose stencil interpolates population k = 1..8 of node i
+        (original numbering relative to the segment)."""
+        ns = int(self.offsets[seg + 1] - self.offsets[seg])
+        out = np.zeros((8, ns), np.int32)
+        _check(lib().mlbm_cloud_departure_nodes(self._h, seg, out.ctypes.data))
         return out
 
     def bounce_mask(self):

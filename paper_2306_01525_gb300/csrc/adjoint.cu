@@ -377,6 +377,8 @@ int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtyp
     if (lam_next == lam_prev) return fail(MLBM_EINVAL, "lam_next and lam_prev must not alias");
     int rc = check_dtype(w, dtype);
     if (rc) return rc;
+    if (w->any_nearest)
+        return fail(MLBM_EINVAL, "the adjoint step supports own-stencil segments only (MLBM_STENCIL_OWN)");
     mlbm_weights *wm = const_cast<mlbm_weights *>(w);
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = set_params(wm, params, st))) return rc;

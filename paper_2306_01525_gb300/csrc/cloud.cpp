@@ -125,9 +125,8 @@ struct Grid {
 };
 
 // K nearest nodes of query node q (segment-local stored index) by (d^2, original index).
-void knn_query(const Grid &g, const double *x, const double *y, const int64_t *orig, int64_t q,
+void knn_query(const Grid &g, const double *x, const double *y, const int64_t *orig, double qx, double qy,
                int K, int32_t *out_local) {
-    double qx = x[q], qy = y[q];
     double bd[kMaxK];
     int64_t bo[kMaxK];
     int32_t bl[kMaxK];
@@ -216,6 +215,8 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
                         "degree out of range or more monomials than stencil nodes in segment " +
                             std::to_string(s));
         if (!(d.dx_ml > 0)) return fail(MLBM_EINVAL, "dx_ml must be > 0");
+        if (d.stencil_mode != MLBM_STENCIL_OWN && d.stencil_mode != MLBM_STENCIL_NEAREST)
+            return fail(MLBM_EINVAL, "unknown stencil mode");
         if (d.geometry == MLBM_GEOM_PERIODIC) {
             if (!(d.lx > 0 && d.ly > 0)) return fail(MLBM_EINVAL, "periodic box needs lx, ly > 0");
         } else if (d.geometry == MLBM_GEOM_ANNULUS) {
@@ -244,6 +245,7 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
         c->mask.assign(n, 0);
         c->fdir.assign(2 * n, 0.0);
         c->node_seg.resize(n);
+        c->near.resize((size_t)8 * n);
         c->csr_ptr.assign(n + 1, 0);
         c->csr_ent.resize(idx_total);
         int64_t io = 0, wo = 0;
@@ -313,11 +315,27 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
             parallel_for(ns, [&](int64_t b, int64_t e) {
                 int32_t tmp[kMaxK];
                 for (int64_t i = b; i < e; ++i) {
-                    knn_query(g, sxp, syp, orig, i, K, tmp);
+                    knn_query(g, sxp, syp, orig, sxp[i], syp[i], K, tmp);
                     if (tmp[0] != (int32_t)i) dup = 1;
                     for (int j = 0; j < K; ++j) idx[(int64_t)j * ns + i] = (int32_t)(o + tmp[j]);
                 }
             });
+            // departure nodes: the node nearest to x_i - e_k dx_ml (Sec. 2.3, appendix algorithm)
+            if (d.stencil_mode == MLBM_STENCIL_NEAREST) {
+                int32_t *near = &c->near[(size_t)8 * o];
+                parallel_for(ns, [&](int64_t b, int64_t e) {
+                    int32_t nn[1];
+                    for (int64_t i = b; i < e; ++i)
+                        for (int k = 1; k < kQ; ++k) {
+                            knn_query(g, sxp, syp, orig, sxp[i] - kEx[k] * d.dx_ml, syp[i] - kEy[k] * d.dx_ml, 1, nn);
+                            near[(int64_t)(k - 1) * ns + i] = (int32_t)(o + nn[0]);
+                        }
+                });
+            } else {
+                int32_t *near = &c->near[(size_t)8 * o];
+                for (int k = 1; k < kQ; ++k)
+                    for (int64_t i = 0; i < ns; ++i) near[(int64_t)(k - 1) * ns + i] = (int32_t)(o + i);
+            }
             if (dup.load()) {
                 delete c;
                 return fail(MLBM_EINVAL, "duplicate nodes in segment " + std::to_string(s) +
@@ -372,7 +390,7 @@ extern "C" {
 
 const char *mlbm_last_error(void) { return g_err.c_str(); }
 
-int mlbm_abi_version(void) { return 1; }
+int mlbm_abi_version(void) { return 2; }
 
 int mlbm_build_cloud(const double *xy, int64_t n, const mlbm_segment_desc *segs,
                      const int64_t *seg_offsets, int nseg, mlbm_cloud **out) {
@@ -400,6 +418,19 @@ int mlbm_cloud_stencil(const mlbm_cloud *c, int seg, int32_t *idx_out) {
             int64_t io = c->perm[sh.off + i] - sh.orig_off;
             int64_t member = c->idx[sh.idx_off + (int64_t)j * ns + i];
             idx_out[(int64_t)j * ns + io] = (int32_t)(c->perm[member] - sh.orig_off);
+        }
+    return MLBM_OK;
+}
+
+int mlbm_cloud_departure_nodes(const mlbm_cloud *c, int seg, int32_t *near) {
+    if (!c || !near) return fail(MLBM_EINVAL, "NULL argument");
+    if (seg < 0 || seg >= c->nseg) return fail(MLBM_EINVAL, "segment out of range");
+    const SegmentHost &sh = c->seg[seg];
+    for (int k = 0; k < 8; ++k)
+        for (int64_t i = 0; i < sh.n; ++i) {
+            int64_t io = c->perm[sh.off + i] - sh.orig_off;
+            int64_t L = c->near[(size_t)8 * sh.off + (int64_t)k * sh.n + i];
+            near[(int64_t)k * sh.n + io] = (int32_t)(c->perm[L] - sh.orig_off);
         }
     return MLBM_OK;
 }

@@ -23,8 +23,9 @@ struct LatticeParams {
 };
 
 // One pull step: gather the eight moving populations from the upstream neighbours (periodic
-// wrap), collide (BGK + forcing along +x), store.  One thread per node, rows of the lattice
-// map to consecutive threads so that every gather of a direction is coalesced.
+// wrap), collide (BGK + forcing along +x), store.  2-D launch: threads along x within one
+// lattice row (blockIdx.y = row), so every gather of a direction is a contiguous run of the
+// source row, shifted by at most one element.
 template <typename T>
 __global__ void __launch_bounds__(256) lattice_step_kernel(int64_t nx, int64_t ny, LatticeParams prm,
                                                            const T *__restrict__ fin, T *__restrict__ fout,
@@ -33,17 +34,24 @@ __global__ void __launch_bounds__(256) lattice_step_kernel(int64_t nx, int64_t n
     const T inv_tau = T(1.0 / prm.tau);
     const T rho_ref = std::is_same<T, float>::value ? T(prm.rho0) : T(0);
     const T gx = T(prm.g), gy = T(0);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t iy = i / nx, ix = i - iy * nx;
+    const int64_t iy = blockIdx.y;
+    const int64_t rowm = (iy == 0 ? ny - 1 : iy - 1) * nx;  // row iy - 1
+    const int64_t row0 = iy * nx;
+    const int64_t rowp = (iy == ny - 1 ? 0 : iy + 1) * nx;  // row iy + 1
+    for (int64_t ix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; ix < nx; ix += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t xm = ix == 0 ? nx - 1 : ix - 1, xp = ix == nx - 1 ? 0 : ix + 1;
+        const int64_t i = row0 + ix;
         T f[9];
-        f[0] = fin[i];
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
-            int64_t sx = ix - ex_of(k), sy = iy - ey_of(k);
-            sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-            sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
-            f[k] = fin[(int64_t)k * N + sy * nx + sx];
-        }
+        // source of population k at (ix, iy) is (ix - ex_k, iy - ey_k)
+        f[0] = __ldg(fin + i);
+        f[1] = __ldg(fin + 1 * N + row0 + xm);
+        f[2] = __ldg(fin + 2 * N + rowm + ix);
+        f[3] = __ldg(fin + 3 * N + row0 + xp);
+        f[4] = __ldg(fin + 4 * N + rowp + ix);
+        f[5] = __ldg(fin + 5 * N + rowm + xm);
+        f[6] = __ldg(fin + 6 * N + rowm + xp);
+        f[7] = __ldg(fin + 7 * N + rowp + xp);
+        f[8] = __ldg(fin + 8 * N + rowp + xm);
         T rho, ux, uy;
         if constexpr (std::is_same<T, float>::value)
             collide_projected(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
@@ -124,15 +132,16 @@ int mlbm_lattice_step(int64_t nx, int64_t ny, const mlbm_params *params, int dty
     if (rc) return rc;
     if (!f_in || !f_out) return fail(MLBM_EINVAL, "NULL argument");
     if (f_in == f_out) return fail(MLBM_EINVAL, "f_in and f_out must not alias");
-    const int64_t N = nx * ny;
     LatticeParams prm{params->tau, params->g, params->rho0};
     cudaStream_t st = (cudaStream_t)stream;
+    if (ny > 65535) return fail(MLBM_EINVAL, "lattice step supports ny <= 65535");
+    const dim3 grid((unsigned)std::min<int64_t>((nx + 255) / 256, 1 << 16), (unsigned)ny);
     if (dtype == MLBM_F32)
-        lattice_step_kernel<float><<<lattice_grid((const void *)lattice_step_kernel<float>, N), 256, 0, st>>>(
-            nx, ny, prm, (const float *)f_in, (float *)f_out, (float *)moments);
+        lattice_step_kernel<float><<<grid, 256, 0, st>>>(nx, ny, prm, (const float *)f_in, (float *)f_out,
+                                                         (float *)moments);
     else
-        lattice_step_kernel<double><<<lattice_grid((const void *)lattice_step_kernel<double>, N), 256, 0, st>>>(
-            nx, ny, prm, (const double *)f_in, (double *)f_out, (double *)moments);
+        lattice_step_kernel<double><<<grid, 256, 0, st>>>(nx, ny, prm, (const double *)f_in, (double *)f_out,
+                                                          (double *)moments);
     return cuda_check_step(cudaGetLastError(), "lattice_step launch");
 }
 

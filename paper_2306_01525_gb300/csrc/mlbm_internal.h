@@ -46,6 +46,7 @@ struct mlbm_cloud_impl {
     std::vector<int32_t> csr_ptr;       // [N+1] transposed stencil row pointers (global)
     std::vector<int32_t> csr_ent;       // entries e = j * n_seg + i_local (segment-local)
     std::vector<int32_t> node_seg;      // stored position -> segment
+    std::vector<int32_t> near;          // per segment [8][n]: departure node of (i, k), stored positions
     int64_t idx_total = 0, w_total = 0;
 };
 
@@ -68,12 +69,16 @@ struct TileDev {
     int64_t begin;  // first stored position
     int64_t w_off;    // element offset of the tile's FP32 shape vectors (members 1..K-1)
     int64_t w64_off;  // element offset of the tile's FP64 shape vectors (members 0..K-1)
-    int64_t l_off;  // offset of the tile's packed slot pairs ([ceil((K-1)/2)][kTileNodes] uint32)
+    int64_t l_off;  // offset of the tile's packed slot pairs: own mode [ceil((K-1)/2)][B] for
+                    // members 1..K-1; nearest mode [8][ceil(K/2)][B] for members 0..K-1 of the
+                    // departure node's stencil, per direction
     int64_t h_off;  // offset of the tile's halo list (int32 stored positions)
     int32_t count;  // nodes in tile
     int32_t seg;    // segment index
     int32_t K;      // stencil size of the segment
     int32_t U;      // halo size (slots)
+    int32_t mode;   // MLBM_STENCIL_OWN or MLBM_STENCIL_NEAREST
+    int32_t pad;
 };
 
 struct GraphKey {
@@ -123,6 +128,12 @@ struct mlbm_weights_impl {
     int num_sms = 0;
     int step_grid[2] = {0, 0};  // persistent grid of the step kernel, [FP32, FP64]
     int solve_wpb = 0;          // warps per CTA the solver ran with (autotuned)
+    bool any_nearest = false;   // some segment interpolates in departure-node stencils
+    // solver system table during the build (nearest-node stencils), freed afterwards
+    int32_t *d_sys_node = nullptr;
+    double *d_sys_q = nullptr;
+    int32_t *d_sys_tgt = nullptr;
+    int64_t nsys = 0;
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
 };

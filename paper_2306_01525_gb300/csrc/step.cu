@@ -105,6 +105,52 @@ __device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const d
     d[1] = c.y + a.y;
 }
 
+// Nearest-node stencils (Sec. 2.3, appendix algorithm): population k of node b is interpolated
+// in the stencil of its departure node L_k, so every direction has its own members; their halo
+// slots are packed [8][ceil(K/2)][B], member 0 being L_k itself.  Same forms as the own-stencil
+// path: FP32 differences to the centre value f_k(L_k) (members 1..K-1), FP64 the literal sum.
+template <typename T, int B>
+__device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileDev &tile, int b,
+                                               const T *__restrict__ shs, T (&f)[9]) {
+    using VT = typename V<T>::type;
+    constexpr bool kLiteral = !std::is_same<T, float>::value;
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;
+    const int K = tile.K, JP = (K + 1) / 2;
+    const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+    const VT *__restrict__ wbase = reinterpret_cast<const VT *>(a.wt + (kLiteral ? tile.w64_off : tile.w_off)) + b;
+    T acc[8], c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t pr = __ldcs(lp + (int64_t)(k * JP) * B);
+        c[k] = shs[(int)(pr & 0xFFFFu) * 8 + k];
+        acc[k] = T(0);
+    }
+    for (int jp = 0; jp < JP; ++jp) {
+        uint32_t pr[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pr[k] = __ldcs(lp + (int64_t)(k * JP + jp) * B);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * jp + h;
+            if (j >= K) break;
+            if (!kLiteral && j == 0) continue;
+            const VT *__restrict__ wr = wbase + (int64_t)(kLiteral ? j : j - 1) * NV * B;
+            T wk[8];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vunpack(wk + q * W, __ldcs(wr + (int64_t)q * B));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int sl = h ? (int)(pr[k] >> 16) : (int)(pr[k] & 0xFFFFu);
+                const T x = shs[sl * 8 + k];
+                acc[k] = kLiteral ? fma(wk[k], x, acc[k]) : fma(wk[k], x - c[k], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k + 1] = kLiteral ? acc[k] : c[k] + acc[k];
+}
+
 // One fused time step over all tiles (persistent CTAs, one node per thread, B threads per CTA
 // and B nodes per tile):
 //   1. stage f^post_k (k = 1..8) of the tile's halo in shared memory as [slot][8];
@@ -137,6 +183,11 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
         const int b = threadIdx.x;
         if (b < tile.count) {
             const int64_t p = tile.begin + b;
+            T f[9];
+            f[0] = a.fin[p];
+            if (tile.mode == MLBM_STENCIL_NEAREST) {
+                interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
+            } else {
             VT c[NV], acc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -179,8 +230,6 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
                 for (int q = 0; q < NV; ++q)
                     vfma<kLiteral>(acc[q], __ldcs(wp + (int64_t)(j * NV + q) * B), sh[s0 * NV + q], c[q]);
             }
-            T f[9];
-            f[0] = a.fin[p];
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 if constexpr (kLiteral)
@@ -188,6 +237,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
                 else
                     vunpack_sum(f + 1 + q * W, c[q], acc[q]);
             }
+            }  // own-stencil interpolation
             // 3. wall bounce-back: unknown populations take the streamed opposite population
             if (a.mask) {
                 const uint16_t mb = a.mask[p];

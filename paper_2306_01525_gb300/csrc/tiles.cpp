@@ -1,7 +1,9 @@
 // Tile tables of the fused step: for each run of B (kTileNodes or kTileNodesSmall) stored nodes of one segment, the
 // halo of nodes its stencils read (own nodes first, then the others sorted), and the 16-bit halo
 // slot of every stencil member j = 1..K-1 (member 0 is the node itself, Sec. 2.2), packed two per
-// 32-bit word as [ceil((K-1)/2)][B].
+// 32-bit word as [ceil((K-1)/2)][B].  In nearest-node mode each direction k has its own stencil
+// (that of the node nearest to the departure point, Sec. 2.3): slots of all K members per
+// direction, [8][ceil(K/2)][B].
 #include <algorithm>
 #include <string>
 #include <thread>
@@ -23,12 +25,16 @@ int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::ve
             t.count = (int32_t)std::min<int64_t>(B, h.n - b);
             t.seg = s;
             t.K = h.K;
+            t.mode = h.d.stencil_mode;
             t.w_off = w_off;
             t.w64_off = w64_off;
             t.l_off = l_off;
             w_off += (int64_t)(h.K - 1) * 8 * B;
             w64_off += (int64_t)h.K * 8 * B;
-            l_off += (int64_t)((h.K - 1 + 1) / 2) * B;
+            if (t.mode == MLBM_STENCIL_NEAREST)
+                l_off += (int64_t)8 * ((h.K + 1) / 2) * B;
+            else
+                l_off += (int64_t)((h.K - 1 + 1) / 2) * B;
             tiles.push_back(t);
         }
     }
@@ -46,12 +52,21 @@ int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::ve
             const SegmentHost &h = c->seg[T.seg];
             const int32_t *idx = &c->idx[h.idx_off];
             const int64_t il0 = T.begin - h.off;
+            const int32_t *near = &c->near[(size_t)8 * h.off];
+            const bool nearest = T.mode == MLBM_STENCIL_NEAREST;
+            // member j of the stencil that interpolates direction k (1..8) at tile node b
+            auto member = [&](int k, int j, int b) -> int32_t {
+                if (!nearest) return idx[(int64_t)j * h.n + il0 + b];
+                const int64_t L = near[(int64_t)(k - 1) * h.n + il0 + b] - h.off;
+                return idx[(int64_t)j * h.n + L];
+            };
             others.clear();
-            for (int j = 1; j < T.K; ++j)
-                for (int b = 0; b < T.count; ++b) {
-                    int32_t m = idx[(int64_t)j * h.n + il0 + b];
-                    if (m < T.begin || m >= T.begin + T.count) others.push_back(m);
-                }
+            for (int k = 1; k <= (nearest ? 8 : 1); ++k)
+                for (int j = nearest ? 0 : 1; j < T.K; ++j)
+                    for (int b = 0; b < T.count; ++b) {
+                        int32_t m = member(k, j, b);
+                        if (m < T.begin || m >= T.begin + T.count) others.push_back(m);
+                    }
             std::sort(others.begin(), others.end());
             others.erase(std::unique(others.begin(), others.end()), others.end());
             std::vector<int32_t> &H = halos[t];
@@ -67,12 +82,24 @@ int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::ve
                 if (m >= T.begin && m < T.begin + T.count) return (uint32_t)(m - T.begin);
                 return (uint32_t)(T.count + (std::lower_bound(others.begin(), others.end(), m) - others.begin()));
             };
-            for (int j = 1; j < T.K; ++j) {
-                const int jp = (j - 1) >> 1, hi = (j - 1) & 1;
-                for (int b = 0; b < T.count; ++b) {
-                    uint32_t sl = slot(idx[(int64_t)j * h.n + il0 + b]);
-                    lidx[T.l_off + (int64_t)jp * B + b] |= hi ? (sl << 16) : sl;
+            if (!nearest) {
+                for (int j = 1; j < T.K; ++j) {
+                    const int jp = (j - 1) >> 1, hi = (j - 1) & 1;
+                    for (int b = 0; b < T.count; ++b) {
+                        uint32_t sl = slot(member(0, j, b));
+                        lidx[T.l_off + (int64_t)jp * B + b] |= hi ? (sl << 16) : sl;
+                    }
                 }
+            } else {
+                const int JP = (T.K + 1) / 2;
+                for (int k = 1; k <= 8; ++k)
+                    for (int j = 0; j < T.K; ++j) {
+                        const int jp = j >> 1, hi = j & 1;
+                        for (int b = 0; b < T.count; ++b) {
+                            uint32_t sl = slot(member(k, j, b));
+                            lidx[T.l_off + ((int64_t)(k - 1) * JP + jp) * B + b] |= hi ? (sl << 16) : sl;
+                        }
+                    }
             }
         }
     };

@@ -75,8 +75,15 @@ struct SolveArgs {
     const int32_t *node_seg;
     double *w64;  // canonical [8][K][n] per segment
     unsigned long long *nbad;
-    int64_t N;
-    int slot;  // doubles per warp slot
+    int64_t N;  // systems
+    int slot;   // doubles per warp slot
+    // optional system table (nearest-node stencils): system s factorises the stencil of node
+    // sys_node[s] and solves for 8 evaluation points sys_q[s][c] (relative to that node,
+    // physical units), writing column c to (node, direction) sys_tgt[s][c] = 8 i + k - 1 (or -1).
+    // Without it system s is node s with the points -e_k dx_ml of its own 8 directions.
+    const int32_t *sys_node;
+    const double *sys_q;
+    const int32_t *sys_tgt;
 };
 
 __device__ __forceinline__ int ld_of(int n) { return (n + 8) | 1; }
@@ -87,8 +94,8 @@ __global__ void solve_kernel(SolveArgs a) {
     const int warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     double *A = sm + (size_t)warp * a.slot;
-    for (int64_t node = (int64_t)blockIdx.x * wpb + warp; node < a.N;
-         node += (int64_t)gridDim.x * wpb) {
+    for (int64_t sys = (int64_t)blockIdx.x * wpb + warp; sys < a.N; sys += (int64_t)gridDim.x * wpb) {
+        const int64_t node = a.sys_node ? (int64_t)a.sys_node[sys] : sys;
         const SegDev sd = a.seg[a.node_seg[node]];
         const int K = sd.K, m = sd.m, n = K + m, ld = ld_of(n), nc = n + 8;
         double *tx = A + n * ld;
@@ -119,6 +126,16 @@ __global__ void solve_kernel(SolveArgs a) {
         __syncwarp();
         // augmented matrix [Phi_L | phi_L(q_1) ... phi_L(q_8)], q_k = -e_k dx_ml / s
         const double dq = sd.dx_ml * is;
+        // evaluation point of right-hand side c in scaled coordinates
+        auto qpt = [&](int c, double &qx, double &qy) {
+            if (a.sys_node) {
+                qx = a.sys_q[(sys * 8 + c) * 2] * is;
+                qy = a.sys_q[(sys * 8 + c) * 2 + 1] * is;
+            } else {
+                qx = -kEx[c + 1] * dq;
+                qy = -kEy[c + 1] * dq;
+            }
+        };
         double amax = 0.0;
         // R block (symmetric: each pair evaluated once), P and P^T blocks, zero block
         for (int e = lane; e < n * n; e += 32) {
@@ -137,13 +154,15 @@ __global__ void solve_kernel(SolveArgs a) {
         }
         // right-hand sides: phi(|q_k - x_j|) and the monomials at q_k
         for (int e = lane; e < 8 * K; e += 32) {
-            const int q = e / K, r = e - q * K, k = q + 1;
-            A[r * ld + n + q] = d_phi(-kEx[k] * dq - tx[r], -kEy[k] * dq - ty[r]);
+            const int q = e / K, r = e - q * K;
+            double qx, qy;
+            qpt(q, qx, qy);
+            A[r * ld + n + q] = d_phi(qx - tx[r], qy - ty[r]);
         }
         if (lane < 8) {
-            const int k = lane + 1;
-            double mq[kMaxMono];
-            d_monomials(sd.deg, -kEx[k] * dq, -kEy[k] * dq, mq);
+            double qx, qy, mq[kMaxMono];
+            qpt(lane, qx, qy);
+            d_monomials(sd.deg, qx, qy, mq);
             for (int l = 0; l < m; ++l) A[(K + l) * ld + n + lane] = mq[l];
         }
         for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
@@ -230,10 +249,10 @@ __global__ void solve_kernel(SolveArgs a) {
             double err = 0.0;
             for (int t = lane; t < 8 * m; t += 32) {
                 int q = t / m, l = t - q * m;
-                int k = q + 1;
-                double acc = 0.0;
+                double acc = 0.0, qx, qy;
+                qpt(q, qx, qy);
                 for (int j = 0; j < K; ++j) acc = fma(A[j * ld + n + q], M[j * m + l], acc);
-                err = fmax(err, fabs(acc - d_mono(l, -kEx[k] * dq, -kEy[k] * dq)));
+                err = fmax(err, fabs(acc - d_mono(l, qx, qy)));
             }
             for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
             bad = !(err <= 1e-8);
@@ -241,9 +260,15 @@ __global__ void solve_kernel(SolveArgs a) {
         if (bad && lane == 0) atomicAdd(a.nbad, 1ULL);
         for (int e = lane; e < 8 * K; e += 32) {
             int q = e / K, j = e - q * K;
+            int64_t ti = il, tk = q;  // own mode: node il, direction q + 1
+            if (a.sys_node) {
+                const int32_t t = a.sys_tgt[sys * 8 + q];
+                if (t < 0) continue;
+                ti = (int64_t)(t >> 3) - sd.off;
+                tk = t & 7;
+            }
             double v = bad ? 0.0 : A[j * ld + n + q];
-            int64_t off = sd.w_off + ((int64_t)q * K + j) * sd.n + il;
-            a.w64[off] = v;
+            a.w64[sd.w_off + (tk * K + j) * sd.n + ti] = v;
         }
         __syncwarp();
     }
@@ -371,6 +396,9 @@ static int launch_solve(mlbm_weights *w, const double *d_x, const double *d_y, u
     a.nbad = d_bad;
     a.N = count;
     a.slot = sh.slot;
+    a.sys_node = w->d_sys_node;
+    a.sys_q = w->d_sys_q;
+    a.sys_tgt = w->d_sys_tgt;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel, 32 * wpb, smem);
     const int64_t need = (count + wpb - 1) / wpb;
@@ -398,7 +426,8 @@ static int tune_warps(mlbm_weights *w, const double *d_x, const double *d_y, uns
         }
     if (!*best_wpb) return fail(MLBM_EINVAL, "collocation system too large for shared memory");
     constexpr int64_t kTuneMin = 200000;
-    if (w->N < kTuneMin) return MLBM_OK;
+    const int64_t nsys = w->d_sys_node ? w->nsys : w->N;
+    if (nsys < kTuneMin) return MLBM_OK;
     {
         std::lock_guard<std::mutex> lk(cache_mu);
         auto it = cache.find(sh.nmax);
@@ -411,7 +440,7 @@ static int tune_warps(mlbm_weights *w, const double *d_x, const double *d_y, uns
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    const int64_t sample = std::min<int64_t>(w->N, (int64_t)w->num_sms * 96);
+    const int64_t sample = std::min<int64_t>(nsys, (int64_t)w->num_sms * 96);
     for (int wpb : {1, 2, 4, 8, 12, 16}) {
         if (!fits(wpb)) continue;
         int rc = launch_solve(w, d_x, d_y, d_bad, sample, wpb, st);  // warm the configuration
@@ -440,6 +469,57 @@ static int tune_warps(mlbm_weights *w, const double *d_x, const double *d_y, uns
     return MLBM_OK;
 }
 
+// System table of a cloud with nearest-node stencils: every departure point x_i - e_k dx_ml
+// is assigned to the node L whose stencil interpolates it; the points of each L are solved
+// against L's factorised collocation matrix in groups of up to eight right-hand sides.
+static void build_systems(const mlbm_cloud *c, std::vector<int32_t> &node, std::vector<double> &q,
+                          std::vector<int32_t> &tgt) {
+    static const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    static const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    node.clear();
+    q.clear();
+    tgt.clear();
+    auto wrap = [](double d, double L) { return L > 0.0 ? d - L * std::round(d / L) : d; };
+    for (int s = 0; s < c->nseg; ++s) {
+        const SegmentHost &h = c->seg[s];
+        const double lx = h.d.geometry == MLBM_GEOM_PERIODIC ? h.d.lx : 0.0;
+        const double ly = h.d.geometry == MLBM_GEOM_PERIODIC ? h.d.ly : 0.0;
+        const int32_t *near = &c->near[(size_t)8 * h.off];
+        // pairs (i, k) grouped by their departure node L (counting sort, i then k ascending)
+        std::vector<int64_t> start(h.n + 1, 0);
+        for (int k = 0; k < 8; ++k)
+            for (int64_t i = 0; i < h.n; ++i) start[near[(int64_t)k * h.n + i] - h.off + 1]++;
+        for (int64_t L = 0; L < h.n; ++L) start[L + 1] += start[L];
+        std::vector<int64_t> fill(start.begin(), start.end() - 1);
+        std::vector<int32_t> pairs((size_t)8 * h.n);
+        for (int64_t i = 0; i < h.n; ++i)
+            for (int k = 0; k < 8; ++k) {
+                const int64_t L = near[(int64_t)k * h.n + i] - h.off;
+                pairs[fill[L]++] = (int32_t)(i * 8 + k);
+            }
+        for (int64_t L = 0; L < h.n; ++L)
+            for (int64_t b = start[L]; b < start[L + 1]; b += 8) {
+                node.push_back((int32_t)(h.off + L));
+                for (int c8 = 0; c8 < 8; ++c8) {
+                    if (b + c8 < start[L + 1]) {
+                        const int32_t pr = pairs[b + c8];
+                        const int64_t i = pr >> 3;
+                        const int k = (pr & 7) + 1;
+                        const double Dx = c->x[h.off + i] - ex[k] * h.d.dx_ml;
+                        const double Dy = c->y[h.off + i] - ey[k] * h.d.dx_ml;
+                        q.push_back(wrap(Dx - c->x[h.off + L], lx));
+                        q.push_back(wrap(Dy - c->y[h.off + L], ly));
+                        tgt.push_back((int32_t)((h.off + i) * 8 + (k - 1)));
+                    } else {
+                        q.push_back(0.0);
+                        q.push_back(0.0);
+                        tgt.push_back(-1);
+                    }
+                }
+            }
+    }
+}
+
 // Solve all systems of a weights object (device arrays in place).  warps_per_block <= 0 asks
 // the autotuner.  The number of bad systems is returned through nbad_out.
 int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStream_t st,
@@ -450,7 +530,7 @@ int solve_weights(mlbm_weights *w, const double *d_x, const double *d_y, cudaStr
     int wpb = warps_per_block;
     if (wpb <= 0) rc = tune_warps(w, d_x, d_y, d_bad, st, &wpb);
     if (!rc) rc = cuda_check(cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), st), "memset");
-    if (!rc) rc = launch_solve(w, d_x, d_y, d_bad, w->N, wpb, st);
+    if (!rc) rc = launch_solve(w, d_x, d_y, d_bad, w->d_sys_node ? w->nsys : w->N, wpb, st);
     unsigned long long nbad = 0;
     if (!rc) rc = cuda_check(cudaMemcpyAsync(&nbad, d_bad, sizeof(nbad), cudaMemcpyDeviceToHost, st), "copy");
     if (!rc) rc = cuda_check(cudaStreamSynchronize(st), "solve_kernel");
@@ -592,7 +672,22 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32t, (size_t)w->wt_total, "W32 tiles");
     if (!rc) rc = dev_alloc(&w->d_params, (size_t)4 * c->nseg, "params");
     int64_t nbad = 0;
+    for (auto &h : c->seg) w->any_nearest |= h.d.stencil_mode == MLBM_STENCIL_NEAREST;
+    if (!rc && w->any_nearest) {
+        std::vector<int32_t> sn, stg;
+        std::vector<double> sq;
+        build_systems(c, sn, sq, stg);
+        w->nsys = (int64_t)sn.size();
+        rc = upload(&w->d_sys_node, sn.data(), sn.size(), "system table");
+        if (!rc) rc = upload(&w->d_sys_q, sq.data(), sq.size(), "system table");
+        if (!rc) rc = upload(&w->d_sys_tgt, stg.data(), stg.size(), "system table");
+    }
     if (!rc) rc = solve_weights(w, d_x, d_y, st, 0, &nbad);
+    cudaFree(w->d_sys_node);
+    cudaFree(w->d_sys_q);
+    cudaFree(w->d_sys_tgt);
+    w->d_sys_node = w->d_sys_tgt = nullptr;
+    w->d_sys_q = nullptr;
     if (!rc) rc = repack_weights(w, st);
     cudaFree(d_x);
     cudaFree(d_y);

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_abi_version():
-    assert mlbm.lib().mlbm_abi_version() == 1
+    assert mlbm.lib().mlbm_abi_version() == 2
 
 
 def _periodic(k, deg, dx):
@@ -134,3 +134,24 @@ def test_weights_without_gpu_fail_loudly():
     rc = mlbm.lib().mlbm_build_weights(c.handle, 0, None, ctypes.byref(h), None)
     assert rc == mlbm.ECUDA
     assert not h.value
+
+
+@pytest.mark.parametrize("geometry", ["periodic", "annulus"])
+def test_departure_nodes_match_oracle_nearest_rule(geometry):
+    """Nearest-node stencil mode: the node whose stencil interpolates population k of node i is
+    the node nearest to x_i - e_k dx_ml (Sec. 2.3), as the oracle's paper mode finds it."""
+    if geometry == "periodic":
+        xy = mi.jittered_lattice(20, 0.3, seed=2)
+        seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=16, degree=3, dx_ml=0.1,
+                   stencil_mode=mlbm.STENCIL_NEAREST)
+        box = (1.0, 1.0)
+    else:
+        xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[2000], seed=4)
+        seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=15, degree=2, dx_ml=0.05,
+                   stencil_mode=mlbm.STENCIL_NEAREST)
+        box = (0.0, 0.0)
+    c = mlbm.build_cloud(xy, seg)
+    sidx, _ = oracle.weights(xy, seg["k"], seg["degree"], seg["dx_ml"], box=box, mode="paper")
+    np.testing.assert_array_equal(c.departure_nodes(0), sidx[1:, 0, :])
+    own = mlbm.build_cloud(xy, dict(seg, stencil_mode=mlbm.STENCIL_OWN))
+    assert np.all(own.departure_nodes(0) == np.arange(xy.shape[1])[None, :])

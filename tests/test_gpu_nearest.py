@@ -1,0 +1,153 @@
+"""Nearest-node stencils on the GPU (MLBM_STENCIL_NEAREST): each departure point x_i - e_k dx_ml
+is interpolated in the stencil of the Eulerian node nearest to it (Sec. 2.3, appendix
+algorithm), against the oracle's "paper" mode; and the paper's convergence study at a fixed
+streaming distance (Fig. tgv_conv_P): refining the cloud drives the meshless error onto the
+lattice-LBM error at dx = dx_ml."""
+import numpy as np
+import pytest
+
+import mlbm_inputs as mi
+import oracle
+
+torch = pytest.importorskip("torch")
+mlbm = pytest.importorskip("paper_2306_01525_gb300")
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.as_tensor(a, dtype=torch.float64, device=DEV)
+
+
+def _periodic_nearest(n_side, K, deg, dx, seed):
+    xy = mi.jittered_lattice(n_side, 0.3, seed=seed)
+    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx,
+               stencil_mode=mlbm.STENCIL_NEAREST)
+    cloud = mlbm.build_cloud(xy, seg)
+    return xy, cloud, mlbm.build_weights(cloud)
+
+
+@pytest.mark.parametrize("n_side,K,deg,ratio", [(24, 16, 2, 2.5), (20, 25, 4, 1.5)])
+def test_nearest_weights_and_departure_nodes_match_oracle(n_side, K, deg, ratio):
+    dx = ratio / n_side
+    xy, cloud, w = _periodic_nearest(n_side, K, deg, dx, seed=7)
+    assert w.n_bad == 0
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode="paper")
+    np.testing.assert_array_equal(cloud.departure_nodes(0), sidx[1:, 0, :])
+    err = np.max(np.abs(w.download(0) - W[1:]))
+    assert err <= {2: 1e-9, 4: 1e-7}[deg], err
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", None)])
+def test_nearest_step_matches_oracle(dtype, tol):
+    """Oracle shape vectors uploaded; FP64 agrees per step to 1e-12, FP32 within 1e-6 relative
+    L2 of the velocity after the run (dx_ml = 2 h: departure points beyond the own stencil)."""
+    n_side, K, deg, dx, tau = 24, 16, 3, 2.0 / 24, 0.8
+    xy, cloud, w = _periodic_nearest(n_side, K, deg, dx, seed=8)
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode="paper")
+    w.upload(W[1:], oracle.stencils(xy, K, box=(1.0, 1.0)).astype(np.int32))
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.02)
+    st = oracle.Stepper(sidx, W, tau)
+    f = oracle.init_equilibrium(rho, u, v)
+    dt = mlbm.F64 if dtype == "f64" else mlbm.F32
+    a = torch.empty(9 * w.n, dtype=torch.float64 if dtype == "f64" else torch.float32, device=DEV)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, dt, _t(rho), _t(u), _t(v), a)
+    perm = cloud.perm()
+    steps = 60
+    for it in range(steps):
+        mlbm.step(w, params, dt, a, b)
+        a, b = b, a
+        f = st.step(f)
+        if dtype == "f64" and it % 10 == 9:
+            post = oracle.collide_field(f, tau)
+            got = np.empty_like(post)
+            got[:, perm] = a.view(9, -1).cpu().numpy()
+            assert np.max(np.abs(got - post)) <= tol * np.max(np.abs(post)), it
+    _, ug, vg = mlbm.moments(w, params, dt, a)
+    _, uo, vo = oracle.moments_field(f)
+    ug, vg = ug.cpu().numpy(), vg.cpu().numpy()
+    err = np.sqrt(np.sum((ug - uo) ** 2 + (vg - vo) ** 2) / np.sum(uo ** 2 + vo ** 2))
+    assert err <= (1e-11 if dtype == "f64" else 1e-6), err
+
+
+def test_nearest_annulus_step_with_walls_matches_oracle():
+    xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[2000], seed=4)
+    dx, K, deg, tau, g = 0.05, 15, 2, 1.0, 1e-5
+    seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=K, degree=deg, dx_ml=dx,
+               stencil_mode=mlbm.STENCIL_NEAREST)
+    cloud = mlbm.build_cloud(xy, seg)
+    w = mlbm.build_weights(cloud)
+    sidx, W = oracle.weights(xy, K, deg, dx, mode="paper")
+    np.testing.assert_array_equal(cloud.departure_nodes(0), sidx[1:, 0, :])
+    w.upload(W[1:], oracle.stencils(xy, K).astype(np.int32))
+    mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
+    force = oracle.azimuthal_force(xy, g)
+    st = oracle.Stepper(sidx, W, tau, mask=mask, force=force)
+    n = xy.shape[1]
+    rng = np.random.default_rng(3)
+    rho, u, v = 1 + 1e-3 * rng.standard_normal(n), 1e-3 * rng.standard_normal(n), 1e-3 * rng.standard_normal(n)
+    params = [(tau, g, 1.0)]
+    a = torch.empty(9 * n, dtype=torch.float64, device=DEV)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F64, _t(rho), _t(u), _t(v), a)
+    f = oracle.init_equilibrium(rho, u, v)
+    perm = cloud.perm()
+    for it in range(20):
+        mlbm.step(w, params, mlbm.F64, a, b)
+        a, b = b, a
+        f = st.step(f)
+    post = oracle.collide_field(f, tau, force)
+    got = np.empty_like(post)
+    got[:, perm] = a.view(9, -1).cpu().numpy()
+    assert np.max(np.abs(got - post)) <= 1e-12 * np.max(np.abs(post))
+
+
+def _tgv_error(n, K, deg, L, u0, tau, steps):
+    xy, cloud, w = _periodic_nearest(n, K, deg, 1.0 / L, seed=60 + n)
+    rho, u, v = mi.tgv_initial(xy, u0)
+    params = [(tau, 0.0, 1.0)]
+    a = torch.empty(9 * w.n, dtype=torch.float64, device=DEV)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F64, _t(rho), _t(u), _t(v), a)
+    res = mlbm.run(w, params, mlbm.F64, a, b, steps)
+    _, um, _ = mlbm.moments(w, params, mlbm.F64, res)
+    ut, _ = oracle.tgv_velocity(xy[0] * L, xy[1] * L, steps, u0=u0, nu=oracle.lattice_viscosity(tau), L=L)
+    return oracle.l2_norm(um.cpu().numpy(), ut)
+
+
+def test_fixed_streaming_distance_converges_to_lattice_lbm_error():
+    """dx_ml = 1/32, Taylor-Green to t_end, N_L = 25: refining the cloud from sqrt(N) = 16 to 128
+    (h/dx_ml from 2 to 1/4) brings the P_4 error down onto the lattice-LBM error at dx = 1/32,
+    and P_4 is more accurate than P_2 on the coarse clouds (oracle on the same inputs:
+    P_4 2.2e-2, 7.0e-3, 6.810e-3, 6.808e-3; lattice LBM 6.808e-3)."""
+    L, tau, u0 = 32, 0.8, 0.01
+    steps = int(round(oracle.tgv_end_time(nu=oracle.lattice_viscosity(tau), L=L)))
+    xy = mi.lattice(L)
+    rho, u, v = mi.tgv_initial(xy, u0)
+    a = torch.empty(9 * L * L, dtype=torch.float64, device=DEV)
+    b = torch.empty_like(a)
+    mom = torch.empty(3 * L * L, dtype=torch.float64, device=DEV)
+    mlbm.lattice_init(L, L, (tau, 0.0, 1.0), mlbm.F64, _t(rho), _t(u), _t(v), a)
+    for _ in range(steps):
+        mlbm.lattice_step(L, L, (tau, 0.0, 1.0), mlbm.F64, a, b, mom)
+        a, b = b, a
+    ut, _ = oracle.tgv_velocity(xy[0] * L, xy[1] * L, steps, u0=u0, nu=oracle.lattice_viscosity(tau), L=L)
+    e_lbm = oracle.l2_norm(mom.view(3, -1)[1].cpu().numpy(), ut)
+    e4 = [_tgv_error(n, 25, 4, L, u0, tau, steps) for n in (16, 32, 64, 128)]
+    e2 = [_tgv_error(n, 25, 2, L, u0, tau, steps) for n in (16, 32)]
+    assert e4[0] > e4[1] > e4[2], e4
+    assert abs(e4[3] - e4[2]) <= 1e-3 * e4[2], e4  # saturated
+    assert abs(e4[-1] - e_lbm) <= 0.01 * e_lbm, (e4, e_lbm)
+    assert e4[0] < e2[0] and e4[1] < e2[1], (e2, e4)
+
+
+def test_adjoint_refuses_nearest_mode():
+    xy, cloud, w = _periodic_nearest(12, 9, 2, 2.0 / 12, seed=9)
+    f = torch.zeros(9 * w.n, dtype=torch.float64, device=DEV)
+    grad = torch.zeros(2, dtype=torch.float64, device=DEV)
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.adjoint_step(w, [(0.8, 0.0, 1.0)], mlbm.F64, f, f.clone(), f.clone(), grad)
+    assert e.value.code == mlbm.EINVAL
