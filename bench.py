@@ -401,6 +401,85 @@ def bench_lattice(n_side: int = 2048, steps: int = 200, warmup: int = 5):
             "dtype": "f32"}
 
 
+def bench_paper_sweep(dtype_name: str = "f64"):
+    """The paper's Taylor-Green convergence study (Sec. 3, Fig. h_dx_explained and
+    Fig. tgv_conv_P) on synthetic clouds: dx_ml in {1/10, 1/40, 1/160} x h in {1/10 .. 1/320} x
+    {P_2, P_4}, N_L = 25, nearest-node stencils, tau = 0.8, dt = 1e-3 (10 dx_ml)^2 (diffusive
+    scaling, U0 = 1, nu = 1), run to t_end; each dx_ml group is one batched cloud stepped by one
+    launch per step.  Also the lattice LBM at dx in {1/10 .. 1/160}.  Returns the L2 map."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    dtype = mlbm.F64 if dtype_name == "f64" else mlbm.F32
+    tdt = torch.float64 if dtype == mlbm.F64 else torch.float32
+    dev = torch.device("cuda", torch.cuda.current_device())
+    td = lambda x: torch.as_tensor(x, dtype=torch.float64, device=dev)
+    tau, nu_lat = 0.8, lattice_nu(0.8)
+    hs = [10, 20, 40, 80, 160, 320]
+    out = {"dx_ml": ["1/10", "1/40", "1/160"], "sqrt_n": hs, "stencil": 25, "dtype": dtype_name,
+           "l2_u": {}, "lbm_l2_u": {}}
+    node_steps, t_all = 0, 0.0
+    for L in (10, 40, 160):
+        steps = int(round(np.log(10.0) * L * L / (2.0 * nu_lat * (2 * np.pi) ** 2)))
+        u0 = 0.01 * 10.0 / L  # U0 dt / dx_ml with dt = 1e-3 (10 dx_ml)^2
+        parts, segs, us, vs = [], [], [], []
+        for deg in (2, 4):
+            for n in hs:
+                xy = mi.jittered_lattice(n, 0.3, seed=1000 + n)
+                parts.append(xy)
+                segs.append(dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=25, degree=deg,
+                                 dx_ml=1.0 / L, stencil_mode=mlbm.STENCIL_NEAREST))
+                _, u, v = mi.tgv_initial(xy, u0)
+                us.append(u)
+                vs.append(v)
+        offs = np.cumsum([0] + [q.shape[1] for q in parts])
+        cloud = mlbm.build_cloud(np.concatenate(parts, axis=1), segs, offs)
+        w = mlbm.build_weights(cloud)
+        N = w.n
+        params = [(tau, 0.0, 1.0)] * len(segs)
+        a = torch.empty(9 * N, dtype=tdt, device=dev)
+        b = torch.empty_like(a)
+        mlbm.init(w, params, dtype, td(np.ones(N)), td(np.concatenate(us)), td(np.concatenate(vs)), a)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = mlbm.run(w, params, dtype, a, b, steps)
+        torch.cuda.synchronize()
+        t_all += time.perf_counter() - t0
+        node_steps += N * steps
+        _, ug, _ = mlbm.moments(w, params, dtype, res)
+        ug = ug.cpu().numpy()
+        decay = np.exp(-2.0 * nu_lat * (2 * np.pi / L) ** 2 * steps)
+        for i, (deg, n) in enumerate([(d, n) for d in (2, 4) for n in hs]):
+            xy = parts[i]
+            ut = u0 * np.cos(2 * np.pi * xy[0]) * np.sin(2 * np.pi * xy[1]) * decay
+            e = float(np.sqrt(np.sum((ug[offs[i]:offs[i + 1]] - ut) ** 2) / np.sum(ut ** 2)))
+            out["l2_u"].setdefault(f"P{deg}", {}).setdefault(f"1/{L}", []).append(e)
+        del w, cloud, a, b, res
+        torch.cuda.empty_cache()
+    for L in (10, 20, 40, 80, 160):
+        steps = int(round(np.log(10.0) * L * L / (2.0 * nu_lat * (2 * np.pi) ** 2)))
+        u0 = 0.01 * 10.0 / L
+        xy = mi.lattice(L)
+        _, u, v = mi.tgv_initial(xy, u0)
+        a = torch.empty(9 * L * L, dtype=tdt, device=dev)
+        b = torch.empty_like(a)
+        mom = torch.empty(3 * L * L, dtype=tdt, device=dev)
+        mlbm.lattice_init(L, L, (tau, 0.0, 1.0), dtype, td(np.ones(L * L)), td(u), td(v), a)
+        for _ in range(steps):
+            mlbm.lattice_step(L, L, (tau, 0.0, 1.0), dtype, a, b, mom)
+            a, b = b, a
+        ul = mom.view(3, -1)[1].double().cpu().numpy()
+        decay = np.exp(-2.0 * nu_lat * (2 * np.pi / L) ** 2 * steps)
+        ut = u0 * np.cos(2 * np.pi * xy[0]) * np.sin(2 * np.pi * xy[1]) * decay
+        out["lbm_l2_u"][f"1/{L}"] = float(np.sqrt(np.sum((ul - ut) ** 2) / np.sum(ut ** 2)))
+    out["value"] = node_steps / t_all / 1e9
+    out["unit"] = UNIT
+    out["seconds"] = t_all
+    return out
+
+
 def _dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -587,6 +666,8 @@ def run_mlbm(args):
         extras["adjoint"] = bench_adjoint(2000)
         torch.cuda.empty_cache()
         extras["lattice_lbm"] = bench_lattice()
+        torch.cuda.empty_cache()
+        extras["paper_sweep"] = bench_paper_sweep("f64")
     line = {
         "metric": METRIC, "value": gnups32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step32, "higher_is_better": True,

@@ -417,11 +417,14 @@ int set_params(mlbm_weights *w, const mlbm_params *params, cudaStream_t st) {
 }
 
 int check_dtype(const mlbm_weights *w, int dtype) {
-    if (dtype == MLBM_F32)
-        return (w->d_w32t && w->step_grid[0]) ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
-    if (dtype == MLBM_F64)
-        return (w->d_w64t && w->step_grid[1]) ? MLBM_OK : fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W64");
-    return fail(MLBM_EINVAL, "dtype must be MLBM_F32 or MLBM_F64");
+    if (dtype != MLBM_F32 && dtype != MLBM_F64) return fail(MLBM_EINVAL, "dtype must be MLBM_F32 or MLBM_F64");
+    const int i = dtype == MLBM_F32 ? 0 : 1;
+    if (!(i == 0 ? (const void *)w->d_w32t : (const void *)w->d_w64t))
+        return fail(MLBM_EINVAL, i == 0 ? "weights built without MLBM_KEEP_W32" : "weights built without MLBM_KEEP_W64");
+    if (!w->step_grid[i])
+        return fail(MLBM_EINVAL, "a tile's halo (" + std::to_string(w->umax) +
+                                     " nodes) does not fit in shared memory at this precision");
+    return MLBM_OK;
 }
 
 template <typename T>
