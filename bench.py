@@ -44,13 +44,15 @@ WORKLOADS = {
 CPU_SAMPLE = dict(n_side=128, K=30, deg=4, tau=0.8, u0=0.01, seed=3)
 
 
-def step_bytes_per_node(K: int, dtype_bytes: int) -> int:
+def step_bytes_per_node(K: int, dtype_bytes: int, nearest: bool = False) -> int:
     """Algorithmic bytes of one node update: the shape-vector entries of the 8 moving
-    directions (FP32: the K - 1 members other than the node itself, whose centre weight follows
-    from constant reproduction; FP64: all K members, the literal sum), K - 1 int32 stencil
-    indices, and the nine populations read once and written once."""
+    directions (FP32: the K - 1 members other than the stencil centre, whose weight follows
+    from constant reproduction; FP64: all K members, the literal sum), the int32 stencil
+    indices (own-node rule: K - 1 shared by all directions; nearest-node rule: K per direction),
+    and the nine populations read once and written once."""
     members = K - 1 if dtype_bytes == 4 else K
-    return 8 * members * dtype_bytes + 4 * (K - 1) + 2 * 9 * dtype_bytes
+    idx = 8 * K * 4 if nearest else 4 * (K - 1)
+    return 8 * members * dtype_bytes + idx + 2 * 9 * dtype_bytes
 
 
 def _peaks():
@@ -181,13 +183,14 @@ def cpu_oracle_gnups(seconds: float, steps=None, warmup: int = 0):
                        f"{el:.1f} s"), done, el
 
 
-def _config(workload, world):
+def _config(workload, world, ratio=1.0, stencil="own"):
     wl = WORKLOADS[workload]
     n_side, K, deg = wl["n_side"], wl["K"], wl["deg"]
     N = n_side * n_side
     return {
         "workload": f"tgv_{n_side}sq_k{K}_d{deg}",
-        "nodes": N, "stencil": K, "degree": deg, "tau": wl["tau"], "u0": wl["u0"], "dx_ml": "h",
+        "nodes": N, "stencil": K, "degree": deg, "tau": wl["tau"], "u0": wl["u0"],
+        "dx_ml": "h" if ratio == 1.0 else f"{ratio}h", "stencil_rule": stencil,
         "geometry": "periodic unit square, lattice jittered +-0.3h",
         "parallelism": "replicas" if world > 1 else "single",
         "l2_flush": "inputs larger than L2 (FP32 shape vectors %.2f GB + 2 states)" % (8 * K * 4 * N / 1e9),
@@ -500,7 +503,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args.workload, 1),
+        "config": _config(args.workload, 1, args.ratio, args.stencil),
         "cpu_baseline": res,
         "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -525,10 +528,11 @@ def run_mlbm(args):
         dist.init_process_group("nccl", device_id=dev)
     wl = WORKLOADS[args.workload]
     n_side, K, deg, tau, u0 = wl["n_side"], wl["K"], wl["deg"], wl["tau"], wl["u0"]
-    dx = 1.0 / n_side
+    dx = args.ratio / n_side
     t0 = time.perf_counter()
     xy = mi.jittered_lattice(n_side, 0.3, seed=wl["seed"])
-    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx)
+    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx,
+               stencil_mode=mlbm.STENCIL_NEAREST if args.stencil == "nearest" else mlbm.STENCIL_OWN)
     cloud = mlbm.build_cloud(xy, seg)
     t_cloud = time.perf_counter() - t0
     torch.cuda.synchronize()
@@ -649,9 +653,10 @@ def run_mlbm(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
-    bpn32 = step_bytes_per_node(K, 4)
+    bpn32 = step_bytes_per_node(K, 4, args.stencil == "nearest")
     achieved = bpn32 * N / (ms_step32 * 1e-3) / 1e9
-    traffic = _ncu_traffic("f32")
+    default_workload = args.workload == "tgv_large" and args.stencil == "own" and args.ratio == 1.0
+    traffic = _ncu_traffic("f32") if default_workload else None
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_gnups(args.cpu_seconds)
@@ -672,7 +677,7 @@ def run_mlbm(args):
         "metric": METRIC, "value": gnups32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step32, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": _config(args.workload, world),
+        "config": _config(args.workload, world, args.ratio, args.stencil),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": peak_kind, "algorithmic_bytes_per_node": bpn32},
@@ -684,7 +689,9 @@ def run_mlbm(args):
         "clocks": clk,
         "gpu_launches": args.steps,
         "fp64": {"value": gnups64, "unit": UNIT, "ms_per_step": ms_step64, "steps": s64,
-                 "achieved_gbs": step_bytes_per_node(K, 8) * N / (ms_step64 * 1e-3) / 1e9},
+                 "achieved_gbs": step_bytes_per_node(K, 8, args.stencil == "nearest") * N / (ms_step64 * 1e-3) / 1e9,
+                 "bound": "fp64 alu", "achieved_tflops": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12,
+                 "peak_tflops": 1.25, "frac": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12 / 1.25},
         "speedup_fp32_vs_fp64": gnups32 / gnups64,
         "fp32_vs_fp64_rel_l2_u": err, "error_steps": args.err_steps,
         "setup_s": {"cloud_host": t_cloud, "weights_gpu": t_weights},
@@ -707,6 +714,12 @@ def main():
     ap.add_argument("--err-steps", type=int, default=10000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stencil", default="own", choices=["own", "nearest"],
+                    help="stencil rule of the main workload (own-node or nearest-node)")
+    ap.add_argument("--ratio", type=float, default=1.0, help="dx_ml / h of the main workload")
+    ap.add_argument("--leg", default=None,
+                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "paper_sweep"],
+                    help="run only this extra measurement and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep, annulus and adjoint measurements")
     args = ap.parse_args()
@@ -714,6 +727,15 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        legs = {"batched": lambda: bench_batched(1000), "annulus": bench_annulus,
+                "adjoint": lambda: bench_adjoint(2000), "lattice_lbm": bench_lattice,
+                "paper_sweep": lambda: bench_paper_sweep("f64")}
+        print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
+        return 0
     return run_mlbm(args)
 
 
