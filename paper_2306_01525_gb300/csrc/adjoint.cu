@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                     if (mb >> k & 1u) f[k] = g[opp_of(k)];
             }
             const double *pr = a.params + 4 * tile.seg;
-            const T tau = T(pr[0]), inv_tau = T(1.0 / pr[0]);
+            const T tau = T(pr[0]), inv_tau = T(pr[3]);
             const T rho_ref = kDev ? T(pr[2]) : T(0);
             T drho, rho, ux, uy;
             moments_of<T>(f, rho_ref, drho, rho, ux, uy);

@@ -70,7 +70,7 @@ struct TileDev {
     int64_t w_off;    // element offset of the tile's FP32 shape vectors (members 1..K-1)
     int64_t w64_off;  // element offset of the tile's FP64 shape vectors (members 0..K-1)
     int64_t l_off;  // offset of the tile's packed slot pairs: own mode [ceil((K-1)/2)][B] for
-                    // members 1..K-1; nearest mode [8][ceil(K/2)][B] for members 0..K-1 of the
+                    // members 1..K-1; nearest mode [ceil(K/2)][B][8] for members 0..K-1 of the
                     // departure node's stencil, per direction
     int64_t h_off;  // offset of the tile's halo list (int32 stored positions)
     int32_t count;  // nodes in tile
@@ -123,7 +123,7 @@ struct mlbm_weights_impl {
     size_t scratch_bytes = 0;
     double *d_partials = nullptr;
     int partial_slots = 0;
-    double *d_params = nullptr;  // [nseg][4] device copy of step parameters
+    double *d_params = nullptr;  // [nseg][4] device copy of step parameters (tau, g, rho0, 1/tau)
     std::vector<double> params_cache;
     int num_sms = 0;
     int step_grid[2] = {0, 0};  // persistent grid of the step kernel, [FP32, FP64]

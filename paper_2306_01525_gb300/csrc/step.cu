@@ -36,7 +36,7 @@ struct StepArgs {
     const T *__restrict__ wt;           // tile layout shape vectors
     const uint16_t *__restrict__ mask;  // NULL when no segment has wall populations
     const T *__restrict__ fdir;         // [2][N]
-    const double *__restrict__ params;  // [nseg][4]: tau, g, rho0, unused
+    const double *__restrict__ params;  // [nseg][4]: tau, g, rho0, 1/tau
     const T *__restrict__ fin;
     T *__restrict__ fout;
     T *__restrict__ mom;  // optional [3][N]
@@ -107,7 +107,7 @@ __device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const d
 
 // Nearest-node stencils (Sec. 2.3, appendix algorithm): population k of node b is interpolated
 // in the stencil of its departure node L_k, so every direction has its own members; their halo
-// slots are packed [8][ceil(K/2)][B], member 0 being L_k itself.  Same forms as the own-stencil
+// slots are packed [ceil(K/2)][B][8], member 0 being L_k itself.  Same forms as the own-stencil
 // path: FP32 differences to the centre value f_k(L_k) (members 1..K-1), FP64 the literal sum.
 template <typename T, int B>
 __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileDev &tile, int b,
@@ -117,19 +117,27 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;
     const int K = tile.K, JP = (K + 1) / 2;
-    const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+    // slot words of a node for one member pair: eight directions, two 16-byte loads
+    const uint4 *__restrict__ lp = reinterpret_cast<const uint4 *>(a.lidx + tile.l_off) + 2 * b;
     const VT *__restrict__ wbase = reinterpret_cast<const VT *>(a.wt + (kLiteral ? tile.w64_off : tile.w_off)) + b;
     T acc[8], c[8];
+    auto load_pairs = [&](int jp, uint32_t (&pr)[8]) {
+        const uint4 lo = __ldcs(lp + (int64_t)jp * 2 * B), hi = __ldcs(lp + (int64_t)jp * 2 * B + 1);
+        pr[0] = lo.x; pr[1] = lo.y; pr[2] = lo.z; pr[3] = lo.w;
+        pr[4] = hi.x; pr[5] = hi.y; pr[6] = hi.z; pr[7] = hi.w;
+    };
+    {
+        uint32_t pr[8];
+        load_pairs(0, pr);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t pr = __ldcs(lp + (int64_t)(k * JP) * B);
-        c[k] = shs[(int)(pr & 0xFFFFu) * 8 + k];
-        acc[k] = T(0);
+        for (int k = 0; k < 8; ++k) {
+            c[k] = shs[(int)(pr[k] & 0xFFFFu) * 8 + k];
+            acc[k] = T(0);
+        }
     }
     for (int jp = 0; jp < JP; ++jp) {
         uint32_t pr[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) pr[k] = __ldcs(lp + (int64_t)(k * JP + jp) * B);
+        load_pairs(jp, pr);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int j = 2 * jp + h;
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
             }
             // 4. collision
             const double *pr = a.params + 4 * tile.seg;
-            const T inv_tau = T(1.0 / pr[0]);
+            const T inv_tau = T(pr[3]);
             const T gm = T(pr[1]);
             T gx = T(0), gy = T(0);
             if (gm != T(0)) {
@@ -403,7 +411,7 @@ int set_params(mlbm_weights *w, const mlbm_params *params, cudaStream_t st) {
         v[4 * s] = params[s].tau;
         v[4 * s + 1] = params[s].g;
         v[4 * s + 2] = params[s].rho0;
-        v[4 * s + 3] = 0.0;
+        v[4 * s + 3] = 1.0 / params[s].tau;  // 1/tau once here, not per node
     }
     if (v == w->params_cache) return MLBM_OK;
     int rc = cuda_check_step(cudaMemcpyAsync(w->d_params, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, st),

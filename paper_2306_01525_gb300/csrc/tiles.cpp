@@ -3,7 +3,7 @@
 // slot of every stencil member j = 1..K-1 (member 0 is the node itself, Sec. 2.2), packed two per
 // 32-bit word as [ceil((K-1)/2)][B].  In nearest-node mode each direction k has its own stencil
 // (that of the node nearest to the departure point, Sec. 2.3): slots of all K members per
-// direction, [8][ceil(K/2)][B].
+// direction, [ceil(K/2)][B][8] so that a node's eight directions are one 32-byte run.
 #include <algorithm>
 #include <string>
 #include <thread>
@@ -97,7 +97,7 @@ int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::ve
                         const int jp = j >> 1, hi = j & 1;
                         for (int b = 0; b < T.count; ++b) {
                             uint32_t sl = slot(member(k, j, b));
-                            lidx[T.l_off + ((int64_t)(k - 1) * JP + jp) * B + b] |= hi ? (sl << 16) : sl;
+                            lidx[T.l_off + ((int64_t)jp * B + b) * 8 + (k - 1)] |= hi ? (sl << 16) : sl;
                         }
                     }
             }
