@@ -20,6 +20,7 @@ namespace {
 
 struct LatticeParams {
     double tau, g, rho0, inv_tau;  // inv_tau = 1 / tau, computed once on the host
+    float g32, rho032, inv_tau32;  // FP32 copies (no per-node conversion on the FP64 unit)
 };
 
 // One pull step: gather the eight moving populations from the upstream neighbours (periodic
@@ -31,9 +32,9 @@ __global__ void __launch_bounds__(256) lattice_step_kernel(int64_t nx, int64_t n
                                                            const T *__restrict__ fin, T *__restrict__ fout,
                                                            T *__restrict__ mom) {
     const int64_t N = nx * ny;
-    const T inv_tau = T(prm.inv_tau);
-    const T rho_ref = std::is_same<T, float>::value ? T(prm.rho0) : T(0);
-    const T gx = T(prm.g), gy = T(0);
+    const T inv_tau = std::is_same<T, float>::value ? T(prm.inv_tau32) : T(prm.inv_tau);
+    const T rho_ref = std::is_same<T, float>::value ? T(prm.rho032) : T(0);
+    const T gx = std::is_same<T, float>::value ? T(prm.g32) : T(prm.g), gy = T(0);
     const int64_t iy = blockIdx.y;
     const int64_t rowm = (iy == 0 ? ny - 1 : iy - 1) * nx;  // row iy - 1
     const int64_t row0 = iy * nx;
@@ -114,7 +115,8 @@ int mlbm_lattice_init(int64_t nx, int64_t ny, const mlbm_params *params, int dty
     if (rc) return rc;
     if (!rho || !ux || !uy || !f_out) return fail(MLBM_EINVAL, "NULL argument");
     const int64_t N = nx * ny;
-    LatticeParams prm{params->tau, params->g, params->rho0, 1.0 / params->tau};
+    LatticeParams prm{params->tau, params->g, params->rho0, 1.0 / params->tau, (float)params->g,
+                      (float)params->rho0, (float)(1.0 / params->tau)};
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == MLBM_F32)
         lattice_init_kernel<float><<<lattice_grid((const void *)lattice_init_kernel<float>, N), 256, 0, st>>>(
@@ -132,7 +134,8 @@ int mlbm_lattice_step(int64_t nx, int64_t ny, const mlbm_params *params, int dty
     if (rc) return rc;
     if (!f_in || !f_out) return fail(MLBM_EINVAL, "NULL argument");
     if (f_in == f_out) return fail(MLBM_EINVAL, "f_in and f_out must not alias");
-    LatticeParams prm{params->tau, params->g, params->rho0, 1.0 / params->tau};
+    LatticeParams prm{params->tau, params->g, params->rho0, 1.0 / params->tau, (float)params->g,
+                      (float)params->rho0, (float)(1.0 / params->tau)};
     cudaStream_t st = (cudaStream_t)stream;
     if (ny > 65535) return fail(MLBM_EINVAL, "lattice step supports ny <= 65535");
     const dim3 grid((unsigned)std::min<int64_t>((nx + 255) / 256, 1 << 16), (unsigned)ny);

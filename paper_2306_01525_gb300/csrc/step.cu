@@ -36,7 +36,7 @@ struct StepArgs {
     const T *__restrict__ wt;           // tile layout shape vectors
     const uint16_t *__restrict__ mask;  // NULL when no segment has wall populations
     const T *__restrict__ fdir;         // [2][N]
-    const double *__restrict__ params;  // [nseg][4]: tau, g, rho0, 1/tau
+    const T *__restrict__ params;  // [nseg][4]: tau, g, rho0, 1/tau in the step's precision
     const T *__restrict__ fin;
     T *__restrict__ fout;
     T *__restrict__ mom;  // optional [3][N]
@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
                 }
             }
             // 4. collision
-            const double *pr = a.params + 4 * tile.seg;
-            const T inv_tau = T(pr[3]);
-            const T gm = T(pr[1]);
+            const T *pr = a.params + 4 * tile.seg;
+            const T inv_tau = pr[3];
+            const T gm = pr[1];
             T gx = T(0), gy = T(0);
             if (gm != T(0)) {
                 gx = gm * a.fdir[p];
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
             }
             T rho, ux, uy;
             if constexpr (std::is_same<T, float>::value)
-                collide_projected(f, T(pr[2]), inv_tau, gx, gy, rho, ux, uy);
+                collide_projected(f, pr[2], inv_tau, gx, gy, rho, ux, uy);
             else
                 collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
             // 5. store
@@ -414,7 +414,13 @@ int set_params(mlbm_weights *w, const mlbm_params *params, cudaStream_t st) {
         v[4 * s + 3] = 1.0 / params[s].tau;  // 1/tau once here, not per node
     }
     if (v == w->params_cache) return MLBM_OK;
-    int rc = cuda_check_step(cudaMemcpyAsync(w->d_params, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+    // device buffer: [nseg][4] float64 followed by an FP32 copy [nseg][4] for the FP32 kernels
+    // (conversions from float64 would run on the FP64 unit once per node)
+    std::vector<double> buf(6 * (size_t)w->nseg, 0.0);
+    std::copy(v.begin(), v.end(), buf.begin());
+    float *f32 = reinterpret_cast<float *>(buf.data() + 4 * (size_t)w->nseg);
+    for (size_t i = 0; i < v.size(); ++i) f32[i] = (float)v[i];
+    int rc = cuda_check_step(cudaMemcpyAsync(w->d_params, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice, st),
                              "parameter upload");
     if (rc) return rc;
     // the pageable source may be read after return: wait for the copy before v dies
@@ -449,7 +455,7 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.wt = std::is_same<T, float>::value ? (const T *)w->d_w32t : (const T *)w->d_w64t;
     a.mask = w->has_mask ? w->d_mask : nullptr;
     a.fdir = std::is_same<T, float>::value ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
-    a.params = w->d_params;
+    a.params = std::is_same<T, float>::value ? (const T *)(w->d_params + 4 * (size_t)w->nseg) : (const T *)w->d_params;
     a.fin = (const T *)fin;
     a.fout = (T *)fout;
     a.mom = (T *)mom;

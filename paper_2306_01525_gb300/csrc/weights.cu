@@ -670,7 +670,7 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     if (!rc) rc = dev_alloc(&w->d_w64, (size_t)w->w_total, "W64");
     if (!rc && (flags & MLBM_KEEP_W64)) rc = dev_alloc(&w->d_w64t, (size_t)w->wt64_total, "W64 tiles");
     if (!rc && (flags & MLBM_KEEP_W32)) rc = dev_alloc(&w->d_w32t, (size_t)w->wt_total, "W32 tiles");
-    if (!rc) rc = dev_alloc(&w->d_params, (size_t)4 * c->nseg, "params");
+    if (!rc) rc = dev_alloc(&w->d_params, (size_t)6 * c->nseg, "params");
     int64_t nbad = 0;
     for (auto &h : c->seg) w->any_nearest |= h.d.stencil_mode == MLBM_STENCIL_NEAREST;
     if (!rc && w->any_nearest) {
