@@ -91,7 +91,7 @@ typedef struct {
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *mlbm_last_error(void);
 
-/* Library ABI version (increments on incompatible changes). */
+/* Library ABI version (increments when entry points are added or changed). */
 int mlbm_abi_version(void);
 
 /* ---------------------------------------------------------------------------------------
@@ -116,6 +116,25 @@ int mlbm_abi_version(void);
 int mlbm_build_cloud(const double *xy, int64_t n, const mlbm_segment_desc *segs,
                      const int64_t *seg_offsets, int nseg, mlbm_cloud **out);
 void mlbm_cloud_free(mlbm_cloud *cloud);
+
+/* ---------------------------------------------------------------------------------------
+ * mlbm_build_cloud_device -- the same stencil build on the GPU (Sec. 2.2 stencils, Sec. 2.3
+ * departure nodes, Sec. 3 periodic search and bounce-back): Morton codes and a stable radix
+ * sort, a bucket grid and one thread per N_L-nearest-neighbour query, departure nodes, masks,
+ * force directions and the transposed stencil, all in kernels.
+ *
+ *   xy, n, segs, seg_offsets, nseg, out   as mlbm_build_cloud (xy is a host pointer).
+ *   stream   CUDA stream for the build; the call synchronises it before returning.
+ *
+ * The result is identical, array for array and bit for bit, to mlbm_build_cloud on the same
+ * arguments: every distance that decides a rank is rounded as the host build rounds it.
+ * Device memory: about 8 (N_L + 10) bytes per node, freed before returning.
+ * Errors: as mlbm_build_cloud, plus MLBM_ECUDA (no device, launch failure) and MLBM_ENOMEM
+ * (device allocation).
+ * ------------------------------------------------------------------------------------- */
+int mlbm_build_cloud_device(const double *xy, int64_t n, const mlbm_segment_desc *segs,
+                            const int64_t *seg_offsets, int nseg, void *stream, mlbm_cloud **out);
+
 
 /* Total node count N of a cloud (-1 if cloud is NULL). */
 int64_t mlbm_cloud_size(const mlbm_cloud *cloud);

@@ -7,7 +7,7 @@ fallback: without the compiled library or a CUDA device the calls raise.
 
 Names follow the C ABI without the ``mlbm_`` prefix:
 
-    build_cloud -> Cloud          host stencil build (Sec. 2.2, Sec. 3)
+    build_cloud -> Cloud          stencil build, host or device=True GPU (Sec. 2.2, 2.3, Sec. 3)
     build_weights -> Weights      batched FP64 shape-vector solve on the GPU (Sec. 2.2-2.3)
     init, step, run               initial state and the fused pull-stream-collide step
     moments, norms                macroscopic fields (eq. macro_var), eq. (L2norm) sums
@@ -72,6 +72,7 @@ def lib():
             L.mlbm_last_error.restype = ctypes.c_char_p
             L.mlbm_abi_version.restype = _c_int
             L.mlbm_build_cloud.argtypes = [_vp, _c_i64, _vp, _vp, _c_int, ctypes.POINTER(_vp)]
+            L.mlbm_build_cloud_device.argtypes = [_vp, _c_i64, _vp, _vp, _c_int, _vp, ctypes.POINTER(_vp)]
             L.mlbm_cloud_free.argtypes = [_vp]
             L.mlbm_cloud_free.restype = None
             L.mlbm_cloud_size.argtypes = [_vp]
@@ -162,9 +163,10 @@ def _params(params, nseg):
 # ----------------------------------------------------------------------------- cloud
 
 class Cloud:
-    """Library-owned node cloud (mlbm_build_cloud)."""
+    """Library-owned node cloud (mlbm_build_cloud, or mlbm_build_cloud_device when device=True:
+    the same cloud, built by kernels on the current CUDA device)."""
 
-    def __init__(self, xy, segments, offsets=None):
+    def __init__(self, xy, segments, offsets=None, device=False, stream=None):
         xy = np.ascontiguousarray(xy, dtype=np.float64)
         if xy.ndim != 2 or xy.shape[0] != 2:
             raise ValueError("xy must have shape (2, n)")
@@ -184,8 +186,12 @@ class Cloud:
                                    float(d.get("r_out", 0.0)), int(d["k"]), int(d["degree"]),
                                    float(d["dx_ml"]), int(d.get("stencil_mode", STENCIL_OWN)))
         h = _vp()
-        _check(lib().mlbm_build_cloud(xy.ctypes.data, n, descs, offs.ctypes.data, nseg,
-                                      ctypes.byref(h)))
+        if device:
+            _check(lib().mlbm_build_cloud_device(xy.ctypes.data, n, descs, offs.ctypes.data, nseg,
+                                                 _stream(stream), ctypes.byref(h)))
+        else:
+            _check(lib().mlbm_build_cloud(xy.ctypes.data, n, descs, offs.ctypes.data, nseg,
+                                          ctypes.byref(h)))
         self._h = h
         self.n = n
         self.nseg = nseg
@@ -227,8 +233,10 @@ class Cloud:
             self._h = None
 
 
-def build_cloud(xy, segments, offsets=None) -> Cloud:
-    return Cloud(xy, segments, offsets)
+def build_cloud(xy, segments, offsets=None, device=False, stream=None) -> Cloud:
+    """Stencil build of a node cloud: on the host, or with device=True on the GPU (identical
+    result)."""
+    return Cloud(xy, segments, offsets, device=device, stream=stream)
 
 
 # ----------------------------------------------------------------------------- weights

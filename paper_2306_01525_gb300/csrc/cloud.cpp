@@ -60,43 +60,12 @@ void parallel_for(int64_t n, F &&fn) {
 }
 
 // Uniform bucket grid over one segment (stored order), for nearest-neighbour queries.
-struct Grid {
-    int ncx = 1, ncy = 1;
-    double x0 = 0, y0 = 0, cw = 1, ch = 1;
-    bool periodic = false;
-    double lx = 0, ly = 0;
+struct Grid : GridGeom {
     std::vector<int32_t> start;  // [ncx*ncy + 1]
     std::vector<int32_t> items;  // segment-local stored indices
 
     void build(const double *x, const double *y, int64_t n, const mlbm_segment_desc &d) {
-        periodic = d.geometry == MLBM_GEOM_PERIODIC;
-        double x1, y1;
-        if (periodic) {
-            lx = d.lx;
-            ly = d.ly;
-            x0 = 0;
-            y0 = 0;
-            x1 = lx;
-            y1 = ly;
-        } else {
-            x0 = *std::min_element(x, x + n);
-            x1 = *std::max_element(x, x + n);
-            y0 = *std::min_element(y, y + n);
-            y1 = *std::max_element(y, y + n);
-            double pad = 1e-9 * std::max(1.0, std::max(x1 - x0, y1 - y0));
-            x0 -= pad;
-            y0 -= pad;
-            x1 += pad;
-            y1 += pad;
-        }
-        double W = std::max(x1 - x0, 1e-300), H = std::max(y1 - y0, 1e-300);
-        // about two nodes per cell; degenerate (thin) clouds get a single row of cells
-        double cells = std::max(1.0, (double)n / 2.0);
-        double csz = std::sqrt(W * H / cells);
-        ncx = (int)std::min(std::min(cells, 32768.0), std::max(1.0, std::floor(W / csz)));
-        ncy = (int)std::min(std::min(cells, 32768.0), std::max(1.0, std::floor(cells / ncx)));
-        cw = W / ncx;
-        ch = H / ncy;
+        static_cast<GridGeom &>(*this) = grid_geom(n, segment_bbox(x, y, n, d), d);
         start.assign((size_t)ncx * ncy + 1, 0);
         std::vector<int32_t> cell(n);
         for (int64_t i = 0; i < n; ++i) {
@@ -195,10 +164,40 @@ void knn_query(const Grid &g, const double *x, const double *y, const int64_t *o
 
 }  // namespace
 
-static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc *segs,
-                            const int64_t *seg_offsets, int nseg, mlbm_cloud **out) {
-    if (!out) return fail(MLBM_EINVAL, "out is NULL");
-    *out = nullptr;
+BBox segment_bbox(const double *x, const double *y, int64_t n, const mlbm_segment_desc &d) {
+    if (d.geometry == MLBM_GEOM_PERIODIC) return BBox{0.0, d.lx, 0.0, d.ly};
+    return BBox{*std::min_element(x, x + n), *std::max_element(x, x + n), *std::min_element(y, y + n),
+                *std::max_element(y, y + n)};
+}
+
+GridGeom grid_geom(int64_t n, const BBox &b, const mlbm_segment_desc &d) {
+    GridGeom g;
+    g.periodic = d.geometry == MLBM_GEOM_PERIODIC;
+    g.lx = g.periodic ? d.lx : 0.0;
+    g.ly = g.periodic ? d.ly : 0.0;
+    double x0 = b.x0, x1 = b.x1, y0 = b.y0, y1 = b.y1;
+    if (!g.periodic) {
+        double pad = 1e-9 * std::max(1.0, std::max(x1 - x0, y1 - y0));
+        x0 -= pad;
+        y0 -= pad;
+        x1 += pad;
+        y1 += pad;
+    }
+    g.x0 = x0;
+    g.y0 = y0;
+    double W = std::max(x1 - x0, 1e-300), H = std::max(y1 - y0, 1e-300);
+    // about two nodes per cell; degenerate (thin) clouds get a single row of cells
+    double cells = std::max(1.0, (double)n / 2.0);
+    double csz = std::sqrt(W * H / cells);
+    g.ncx = (int)std::min(std::min(cells, 32768.0), std::max(1.0, std::floor(W / csz)));
+    g.ncy = (int)std::min(std::min(cells, 32768.0), std::max(1.0, std::floor(cells / g.ncx)));
+    g.cw = W / g.ncx;
+    g.ch = H / g.ncy;
+    return g;
+}
+
+int check_cloud_args(const double *xy, int64_t n, const mlbm_segment_desc *segs, const int64_t *seg_offsets,
+                     int nseg, int64_t *idx_total_out, int64_t *w_total_out) {
     if (!xy || !segs || !seg_offsets || n < 1 || nseg < 1)
         return fail(MLBM_EINVAL, "bad arguments to mlbm_build_cloud");
     if (seg_offsets[0] != 0 || seg_offsets[nseg] != n)
@@ -230,9 +229,14 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
     if (idx_total >= (1LL << 31)) return fail(MLBM_EINVAL, "N_L * N must stay below 2^31");
     for (int64_t i = 0; i < 2 * n; ++i)
         if (!std::isfinite(xy[i])) return fail(MLBM_EINVAL, "non-finite coordinate");
+    *idx_total_out = idx_total;
+    *w_total_out = w_total;
+    return MLBM_OK;
+}
 
-    mlbm_cloud *c = new (std::nothrow) mlbm_cloud();
-    if (!c) return fail(MLBM_ENOMEM, "host allocation failed");
+mlbm_cloud *new_cloud(int64_t n, const mlbm_segment_desc *segs, const int64_t *seg_offsets, int nseg,
+                      int64_t idx_total, int64_t w_total) {
+    mlbm_cloud *c = new mlbm_cloud();
     try {
         c->nseg = nseg;
         c->N = n;
@@ -264,24 +268,31 @@ static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc
             wo += 8LL * sh.K * sh.n;
             c->seg.push_back(sh);
         }
+    } catch (...) {
+        delete c;
+        throw;
+    }
+    return c;
+}
+
+static int build_cloud_impl(const double *xy, int64_t n, const mlbm_segment_desc *segs,
+                            const int64_t *seg_offsets, int nseg, mlbm_cloud **out) {
+    if (!out) return fail(MLBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int64_t idx_total = 0, w_total = 0;
+    int rc = check_cloud_args(xy, n, segs, seg_offsets, nseg, &idx_total, &w_total);
+    if (rc) return rc;
+    mlbm_cloud *c = nullptr;
+    try {
+        c = new_cloud(n, segs, seg_offsets, nseg, idx_total, w_total);
         const double *X = xy, *Y = xy + n;
         for (int s = 0; s < nseg; ++s) {
             SegmentHost &sh = c->seg[s];
             const mlbm_segment_desc &d = sh.d;
             int64_t ns = sh.n, o = sh.off;
             // Morton order of the segment: 16-bit quantised coordinates, interleaved.
-            double x0, x1, y0, y1;
-            if (d.geometry == MLBM_GEOM_PERIODIC) {
-                x0 = 0;
-                y0 = 0;
-                x1 = d.lx;
-                y1 = d.ly;
-            } else {
-                x0 = *std::min_element(X + o, X + o + ns);
-                x1 = *std::max_element(X + o, X + o + ns);
-                y0 = *std::min_element(Y + o, Y + o + ns);
-                y1 = *std::max_element(Y + o, Y + o + ns);
-            }
+            const BBox bb = segment_bbox(X + o, Y + o, ns, d);
+            const double x0 = bb.x0, x1 = bb.x1, y0 = bb.y0, y1 = bb.y1;
             double sx = (x1 > x0) ? 65536.0 / (x1 - x0) : 0.0;
             double sy = (y1 > y0) ? 65536.0 / (y1 - y0) : 0.0;
             std::vector<std::pair<uint64_t, int64_t>> key(ns);
@@ -390,7 +401,7 @@ extern "C" {
 
 const char *mlbm_last_error(void) { return g_err.c_str(); }
 
-int mlbm_abi_version(void) { return 2; }
+int mlbm_abi_version(void) { return 3; }
 
 int mlbm_build_cloud(const double *xy, int64_t n, const mlbm_segment_desc *segs,
                      const int64_t *seg_offsets, int nseg, mlbm_cloud **out) {

@@ -123,7 +123,8 @@ struct mlbm_weights_impl {
     size_t scratch_bytes = 0;
     double *d_partials = nullptr;
     int partial_slots = 0;
-    double *d_params = nullptr;  // [nseg][4] device copy of step parameters (tau, g, rho0, 1/tau)
+    double *d_params = nullptr;  // [nseg][4] step parameters (tau, g, rho0, 1/tau) in FP64, then
+                                 // the same [nseg][4] in FP32 (float view at d_params + 4 nseg)
     std::vector<double> params_cache;
     int num_sms = 0;
     int step_grid[2] = {0, 0};  // persistent grid of the step kernel, [FP32, FP64]
@@ -142,3 +143,31 @@ struct mlbm_weights_impl {
 
 struct mlbm_cloud : mlbm::mlbm_cloud_impl {};
 struct mlbm_weights : mlbm::mlbm_weights_impl {};
+
+namespace mlbm {
+
+// Helpers shared by the host build (cloud.cpp) and the device build (cloud_gpu.cu) of a cloud.
+
+// Argument checks of mlbm_build_cloud; on success the stencil and shape-vector totals.
+int check_cloud_args(const double *xy, int64_t n, const mlbm_segment_desc *segs, const int64_t *seg_offsets,
+                     int nseg, int64_t *idx_total, int64_t *w_total);
+// A cloud with every array sized and the segment table filled (throws std::bad_alloc).
+mlbm_cloud *new_cloud(int64_t n, const mlbm_segment_desc *segs, const int64_t *seg_offsets, int nseg,
+                      int64_t idx_total, int64_t w_total);
+
+// Bounding box of a segment: the periodic box, else the extent of its nodes (unpadded).
+struct BBox {
+    double x0, x1, y0, y1;
+};
+BBox segment_bbox(const double *x, const double *y, int64_t n, const mlbm_segment_desc &d);
+
+// Uniform bucket grid of a segment (about two nodes per cell) for nearest-neighbour queries.
+struct GridGeom {
+    int ncx, ncy;
+    double x0, y0, cw, ch;
+    bool periodic;
+    double lx, ly;
+};
+GridGeom grid_geom(int64_t n, const BBox &b, const mlbm_segment_desc &d);
+
+}  // namespace mlbm

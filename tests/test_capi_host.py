@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_abi_version():
-    assert mlbm.lib().mlbm_abi_version() == 2
+    assert mlbm.lib().mlbm_abi_version() == 3
 
 
 def _periodic(k, deg, dx):
@@ -134,6 +134,26 @@ def test_weights_without_gpu_fail_loudly():
     rc = mlbm.lib().mlbm_build_weights(c.handle, 0, None, ctypes.byref(h), None)
     assert rc == mlbm.ECUDA
     assert not h.value
+
+
+def test_device_cloud_build_without_gpu_fails_loudly():
+    """The device stencil build checks its arguments like the host build, and without a CUDA
+    device returns MLBM_ECUDA (no host fallback)."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    xy = mi.jittered_lattice(8, 0.3, seed=1)
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.build_cloud(xy, _periodic(0, 2, 0.1), device=True, stream=_NullStream())
+    assert e.value.code == mlbm.EINVAL
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.build_cloud(xy, _periodic(9, 2, 0.1), device=True, stream=_NullStream())
+    assert e.value.code == mlbm.ECUDA
+
+
+class _NullStream:
+    cuda_stream = 0
 
 
 @pytest.mark.parametrize("geometry", ["periodic", "annulus"])
