@@ -63,9 +63,10 @@ __device__ __forceinline__ void d_monomials(int deg, double x, double y, double 
         for (int b = 0; b <= t; ++b) out[c++] = px[t - b] * py[b];
 }
 
+// Cubic polyharmonic spline phi(r) = r^3 = r^2 * r.
 __device__ __forceinline__ double d_phi(double dx, double dy) {
-    double r = sqrt(dx * dx + dy * dy);
-    return r * r * r;
+    const double r2 = dx * dx + dy * dy;
+    return r2 * sqrt(r2);
 }
 
 struct SolveArgs {
@@ -136,21 +137,42 @@ __global__ void solve_kernel(SolveArgs a) {
                 qy = -kEy[c + 1] * dq;
             }
         };
-        double amax = 0.0;
-        // R block (symmetric: each pair evaluated once), P and P^T blocks, zero block
-        for (int e = lane; e < n * n; e += 32) {
-            const int r = e / n, c = e - r * n;
-            if (r < K && c < K) {
-                if (r > c) continue;
-                const double v = d_phi(tx[r] - tx[c], ty[r] - ty[c]);
-                A[r * ld + c] = v;
-                A[c * ld + r] = v;
-                amax = fmax(amax, v);
+        // Every FP64 warp instruction costs the same whatever its active lanes (two FP64 lanes
+        // per SM clock on this part), so the fill, pivot search and updates below are laid out
+        // to keep lanes busy and keep comparisons off the FP64 unit: non-negative doubles order
+        // like their bit patterns, so magnitudes are compared as 64-bit integers.
+        const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+        unsigned long long amax = 0;  // bits of max |Phi entry|
+        // R block: each strict upper pair evaluated once, rows a and K-2-a folded into one run of
+        // K pairs; mirrored below the diagonal; phi(0) = 0 on the diagonal
+        const int npair = K * (K - 1) / 2;
+        for (int t = lane; t < npair; t += 32) {
+            const int ra = t / K, b = t - ra * K;
+            int r, c;
+            if (b < K - 1 - ra) {
+                r = ra;
+                c = ra + 1 + b;
             } else {
-                const double v = (r < K) ? M[r * m + (c - K)] : ((c < K) ? M[c * m + (r - K)] : 0.0);
-                A[r * ld + c] = v;
-                amax = fmax(amax, fabs(v));
+                r = K - 2 - ra;
+                c = b;
             }
+            const double v = d_phi(tx[r] - tx[c], ty[r] - ty[c]);
+            A[r * ld + c] = v;
+            A[c * ld + r] = v;
+            amax = max(amax, (unsigned long long)__double_as_longlong(v) & kAbs);
+        }
+        for (int r = lane; r < K; r += 32) A[r * ld + r] = 0.0;
+        // P and P^T blocks, zero block
+        for (int e = lane; e < K * m; e += 32) {
+            const int r = e / m, l = e - r * m;
+            const double v = M[e];
+            A[r * ld + K + l] = v;
+            A[(K + l) * ld + r] = v;
+            amax = max(amax, (unsigned long long)__double_as_longlong(v) & kAbs);
+        }
+        for (int e = lane; e < m * m; e += 32) {
+            const int r = e / m, l = e - r * m;
+            A[(K + r) * ld + K + l] = 0.0;
         }
         // right-hand sides: phi(|q_k - x_j|) and the monomials at q_k
         for (int e = lane; e < 8 * K; e += 32) {
@@ -165,29 +187,32 @@ __global__ void solve_kernel(SolveArgs a) {
             d_monomials(sd.deg, qx, qy, mq);
             for (int l = 0; l < m; ++l) A[(K + l) * ld + n + lane] = mq[l];
         }
-        for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        // pivots must exceed 1e-14 max|Phi| (and be finite)
+        const unsigned long long thr = (unsigned long long)__double_as_longlong(1e-14 * __longlong_as_double((long long)amax));
         __syncwarp();
         bool bad = false;
+        double *invp = M + K * m;  // reciprocal pivots, [n]
         // LU with partial pivoting, eliminating the right-hand sides along
         for (int p = 0; p < n; ++p) {
-            double best = -1.0;
+            unsigned long long best = 0;
             int piv = p;
             for (int r = p + lane; r < n; r += 32) {
-                double v = fabs(A[r * ld + p]);
+                const unsigned long long v = (unsigned long long)__double_as_longlong(A[r * ld + p]) & kAbs;
                 if (v > best) {
                     best = v;
                     piv = r;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                double ob = __shfl_xor_sync(0xffffffffu, best, o);
-                int op = __shfl_xor_sync(0xffffffffu, piv, o);
+                const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int op = __shfl_xor_sync(0xffffffffu, piv, o);
                 if (ob > best || (ob == best && op < piv)) {
                     best = ob;
                     piv = op;
                 }
             }
-            if (!(best > 1e-14 * amax)) {
+            if (!(best > thr) || best >= 0x7FF0000000000000ull) {
                 bad = true;
                 break;
             }
@@ -200,35 +225,62 @@ __global__ void solve_kernel(SolveArgs a) {
             }
             __syncwarp();
             const double inv = 1.0 / A[p * ld + p];
+            if (lane == 0) invp[p] = inv;
             for (int r = p + 1 + lane; r < n; r += 32) A[r * ld + p] *= inv;
             __syncwarp();
-            // trailing update A[r][c] -= l_r A[p][c], rows in groups of four with all loads issued
-            // before the stores (shared memory aliasing would otherwise serialise every row)
-            for (int c = p + 1 + lane; c < nc; c += 32) {
-                const double apc = A[p * ld + c];
-                int r = p + 1;
-                for (; r + 3 < n; r += 4) {
-                    const double l0 = A[r * ld + p], l1 = A[(r + 1) * ld + p];
-                    const double l2 = A[(r + 2) * ld + p], l3 = A[(r + 3) * ld + p];
-                    double a0 = A[r * ld + c], a1 = A[(r + 1) * ld + c];
-                    double a2 = A[(r + 2) * ld + c], a3 = A[(r + 3) * ld + c];
-                    a0 = fma(-l0, apc, a0);
-                    a1 = fma(-l1, apc, a1);
-                    a2 = fma(-l2, apc, a2);
-                    a3 = fma(-l3, apc, a3);
-                    A[r * ld + c] = a0;
-                    A[(r + 1) * ld + c] = a1;
-                    A[(r + 2) * ld + c] = a2;
-                    A[(r + 3) * ld + c] = a3;
+            // trailing update A[r][c] -= l_r A[p][c] over the (n-p-1) x (nc-p-1) block, flattened
+            // row-major across the lanes (element e = lane + 32 t), four elements per pass with
+            // all loads issued before the stores
+            const int C = nc - p - 1, E = (n - p - 1) * C;
+            if (E > 0) {
+                const int dr = 32 / C, dc = 32 - dr * C;
+                int rr = lane / C, cc = lane - rr * C;
+                auto advance = [&](int &r_, int &c_) {
+                    r_ += dr;
+                    c_ += dc;
+                    if (c_ >= C) {
+                        c_ -= C;
+                        ++r_;
+                    }
+                };
+                const double *Ap = A + p * ld + p + 1;   // row p, columns p+1..
+                double *Ab = A + (p + 1) * ld + p + 1;   // block origin (p+1, p+1)
+                const double *Al = A + (p + 1) * ld + p;  // column p, rows p+1..
+                int e = lane;
+                for (; e + 96 < E; e += 128) {
+                    int r0 = rr, c0 = cc, r1 = r0, c1 = c0;
+                    advance(r1, c1);
+                    int r2 = r1, c2 = c1;
+                    advance(r2, c2);
+                    int r3 = r2, c3 = c2;
+                    advance(r3, c3);
+                    const double l0 = Al[r0 * ld], l1 = Al[r1 * ld], l2 = Al[r2 * ld], l3 = Al[r3 * ld];
+                    const double u0 = Ap[c0], u1 = Ap[c1], u2 = Ap[c2], u3 = Ap[c3];
+                    double a0 = Ab[r0 * ld + c0], a1 = Ab[r1 * ld + c1];
+                    double a2 = Ab[r2 * ld + c2], a3 = Ab[r3 * ld + c3];
+                    a0 = fma(-l0, u0, a0);
+                    a1 = fma(-l1, u1, a1);
+                    a2 = fma(-l2, u2, a2);
+                    a3 = fma(-l3, u3, a3);
+                    Ab[r0 * ld + c0] = a0;
+                    Ab[r1 * ld + c1] = a1;
+                    Ab[r2 * ld + c2] = a2;
+                    Ab[r3 * ld + c3] = a3;
+                    rr = r3;
+                    cc = c3;
+                    advance(rr, cc);
                 }
-                for (; r < n; ++r) A[r * ld + c] = fma(-A[r * ld + p], apc, A[r * ld + c]);
+                for (; e < E; e += 32) {
+                    Ab[rr * ld + cc] = fma(-Al[rr * ld], Ap[cc], Ab[rr * ld + cc]);
+                    advance(rr, cc);
+                }
             }
             __syncwarp();
         }
         if (!bad) {
             // back substitution of the eight right-hand sides
             for (int p = n - 1; p >= 0; --p) {
-                if (lane < 8) A[p * ld + n + lane] /= A[p * ld + p];
+                if (lane < 8) A[p * ld + n + lane] *= invp[p];
                 __syncwarp();
                 // lanes over (row, rhs) pairs; rows r = lane/8, lane/8 + 4, ... (four per pass)
                 const int q = lane & 7;
@@ -375,7 +427,7 @@ static SolveShape solve_shape(const mlbm_weights *w) {
     int km = 0;
     for (auto &s : w->seg) km = std::max(km, s.K * s.m);
     const int ld = (nmax + 8) | 1;
-    return SolveShape{nmax * ld + 2 * kmax + km, nmax};
+    return SolveShape{nmax * ld + 2 * kmax + km + nmax, nmax};
 }
 
 // Launch the solver over nodes [0, count) with `wpb` warps (one system each) per CTA.
