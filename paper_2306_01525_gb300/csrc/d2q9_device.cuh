@@ -27,6 +27,9 @@ __host__ __device__ constexpr T omega_of(int k) {
 static_assert(opp_of(1) == 3 && opp_of(2) == 4 && opp_of(3) == 1 && opp_of(4) == 2, "opp");
 static_assert(opp_of(5) == 7 && opp_of(6) == 8 && opp_of(7) == 5 && opp_of(8) == 6, "opp");
 static_assert(ex_of(opp_of(6)) == -ex_of(6) && ey_of(opp_of(6)) == -ey_of(6), "opp");
+// direction pairs of collide(): c_1 = (1,0), c_2 = (0,1), c_5 = (1,1), c_6 = (-1,1)
+static_assert(ex_of(1) == 1 && ey_of(1) == 0 && ex_of(2) == 0 && ey_of(2) == 1, "axes");
+static_assert(ex_of(5) == 1 && ey_of(5) == 1 && ex_of(6) == -1 && ey_of(6) == 1, "diagonals");
 
 // Macroscopic fields of storage-form populations: drho = rho - rho_ref, and rho, u.
 template <typename T>
@@ -49,18 +52,32 @@ __device__ __forceinline__ T geq_of(int k, T drho, T rho, T ux, T uy, T usq15) {
 
 // In place: s <- s - (s - s^eq) / tau + omega_k e_k.g / c_s^2.  Returns the pre-collision
 // moments through rho, ux, uy.
+//
+// Evaluated as s (1 - 1/tau) + s^eq / tau + F_k, direction pairs (k, opposite of k) together:
+// c_k.u and e_k.g change sign between the two, so s^eq / tau splits into a common even part
+// omega (drho + rho (4.5 cu^2 - 1.5 u^2)) / tau and an odd part 3 omega rho cu / tau, and the
+// forcing term (odd as well) joins the odd part.  About half the arithmetic of evaluating the
+// nine equilibria one by one, which matters where FP64 arithmetic bounds the step.
 template <typename T>
 __device__ __forceinline__ void collide(T (&s)[9], T rho_ref, T inv_tau, T gx, T gy, T &rho, T &ux,
                                         T &uy) {
     T drho;
     moments_of(s, rho_ref, drho, rho, ux, uy);
     const T usq15 = T(1.5) * (ux * ux + uy * uy);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        T geq = geq_of<T>(k, drho, rho, ux, uy, usq15);
-        T force = omega_of<T>(k) * T(3) * (T(ex_of(k)) * gx + T(ey_of(k)) * gy);
-        s[k] = s[k] - (s[k] - geq) * inv_tau + force;
-    }
+    const T keep = T(1) - inv_tau;
+    const T dt = drho * inv_tau, rt = rho * inv_tau;
+    s[0] = fma(s[0], keep, omega_of<T>(0) * (dt - rt * usq15));
+    // (k, opposite): c_k.u = cu, e_k.g = eg, weight w
+    auto pair = [&](int k, int ko, T cu, T eg, T w) {
+        const T even = w * fma(rt, fma(T(4.5) * cu, cu, -usq15), dt);
+        const T odd = (T(3) * w) * fma(rt, cu, eg);
+        s[k] = fma(s[k], keep, even + odd);
+        s[ko] = fma(s[ko], keep, even - odd);
+    };
+    pair(1, 3, ux, gx, omega_of<T>(1));
+    pair(2, 4, uy, gy, omega_of<T>(2));
+    pair(5, 7, ux + uy, gx + gy, omega_of<T>(5));
+    pair(6, 8, uy - ux, gy - gx, omega_of<T>(6));
 }
 
 // FP32 collision with exact conservation by construction.  With rounded lattice weights
