@@ -239,6 +239,29 @@ int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, v
              int64_t nsteps, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * mlbm_step_host -- one time step (as mlbm_step) for each of nbatch independent states held
+ * in HOST memory, end to end: state b is copied to the device, stepped, and its new
+ * post-collision state copied back.  Two device buffers per direction and one copy stream per
+ * direction let the copy in of state b + 1 and the copy out of state b - 1 run while state b
+ * steps, so the call is bound by the slower of the host link and the step.
+ *
+ *   w, params, dtype   as mlbm_step.
+ *   nbatch   number of states (>= 1).
+ *   f_in     host, nbatch pointers, each to a [9][N] state of dtype in stored order.
+ *   f_out    host, nbatch pointers receiving the stepped states; f_out[b] may equal f_in[b]
+ *            but must not overlap f_in[c] for c != b.  Inputs may repeat; outputs that
+ *            overlap each other end up holding the later state.
+ *   stream   CUDA stream the steps run on (the copies start after work already queued on it);
+ *            every copy and step has finished when the call returns.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the copies run
+ * asynchronously; pageable memory gives the same results with serialised copies.  Device
+ * memory: four state buffers kept in the weights object for later calls.
+ * Errors: MLBM_EINVAL, MLBM_ENOMEM, MLBM_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+int mlbm_step_host(mlbm_weights *w, const mlbm_params *params, int dtype, int64_t nbatch,
+                   const void *const *f_in, void *const *f_out, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * mlbm_moments -- macroscopic fields (eq. macro_var) of the time level whose post-collision
  * state is f: rho = sum f, rho u = sum f e - g (collision conserves rho and adds exactly the
  * body force g to rho u, so these are the post-streaming moments the paper reports).

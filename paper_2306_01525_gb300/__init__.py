@@ -28,7 +28,7 @@ __all__ = [
     "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
     "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
-    "lattice_init", "lattice_step",
+    "lattice_init", "lattice_step", "step_host",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -90,6 +90,7 @@ def lib():
             L.mlbm_init.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_run.argtypes = [_vp, _vp, _c_int, _vp, _vp, _c_i64, _vp]
+            L.mlbm_step_host.argtypes = [_vp, _vp, _c_int, _c_i64, _vp, _vp, _vp]
             L.mlbm_moments.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_norms.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
             L.mlbm_norms_noalloc.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
@@ -311,6 +312,29 @@ def step(w: Weights, params, dtype, f_in, f_out, moments_out=None, stream=None):
     _check(lib().mlbm_step(w.handle, _params(params, w.nseg), dtype,
                            _state(w, dtype, f_in, "f_in"), _state(w, dtype, f_out, "f_out"),
                            mom, _stream(stream)))
+
+
+def _host_state(w, dtype, t, name):
+    import torch
+
+    want = _torch_dtype(dtype)
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError(f"{name} must be a host (CPU) tensor")
+    if t.dtype != want or t.numel() != 9 * w.n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {want} tensor of 9 * N elements")
+    return t.data_ptr()
+
+
+def step_host(w: Weights, params, dtype, f_in, f_out, stream=None):
+    """One step for each of a batch of independent states in HOST memory (lists of CPU tensors,
+    ideally pinned): copies in, fused step, copies out, pipelined across the batch
+    (mlbm_step_host).  Returns when the results are in f_out."""
+    if len(f_in) != len(f_out) or not f_in:
+        raise ValueError("f_in and f_out must be non-empty lists of the same length")
+    nb = len(f_in)
+    ins = (_vp * nb)(*[_host_state(w, dtype, t, "f_in") for t in f_in])
+    outs = (_vp * nb)(*[_host_state(w, dtype, t, "f_out") for t in f_out])
+    _check(lib().mlbm_step_host(w.handle, _params(params, w.nseg), dtype, nb, ins, outs, _stream(stream)))
 
 
 def run(w: Weights, params, dtype, f_a, f_b, nsteps: int, stream=None):

@@ -137,6 +137,12 @@ struct mlbm_weights_impl {
     int64_t nsys = 0;
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
+    // host-buffer steps (mlbm_step_host): two input and two output state buffers, one copy
+    // stream per direction and their events, created on first use
+    void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t stage_bytes = 0;
+    void *copy_stream[2] = {nullptr, nullptr};  // cudaStream_t: host->device, device->host
+    void *stage_event[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // cudaEvent_t
 };
 
 }  // namespace mlbm

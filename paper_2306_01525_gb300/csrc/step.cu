@@ -619,6 +619,73 @@ int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, v
     return MLBM_OK;
 }
 
+int mlbm_step_host(mlbm_weights *w, const mlbm_params *params, int dtype, int64_t nbatch, const void *const *f_in,
+                   void *const *f_out, void *stream) {
+    set_error("");
+    if (!w || !f_in || !f_out) return fail(MLBM_EINVAL, "NULL argument");
+    if (nbatch < 1) return fail(MLBM_EINVAL, "nbatch < 1");
+    for (int64_t b = 0; b < nbatch; ++b)
+        if (!f_in[b] || !f_out[b]) return fail(MLBM_EINVAL, "NULL state pointer");
+    int rc = check_dtype(w, dtype);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = set_params(w, params, st))) return rc;
+    const size_t bytes = (size_t)9 * w->N * (dtype == MLBM_F32 ? sizeof(float) : sizeof(double));
+    // staging buffers and copy streams, kept for later calls
+    if (w->stage_bytes < bytes) {
+        for (void *&p : w->d_stage) {
+            cudaFree(p);
+            p = nullptr;
+        }
+        w->stage_bytes = 0;
+        for (void *&p : w->d_stage) {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e == cudaErrorMemoryAllocation) {
+                cudaGetLastError();
+                return fail(MLBM_ENOMEM, "device allocation of the host-step buffers failed");
+            }
+            if ((rc = cuda_check_step(e, "host-step buffers"))) return rc;
+        }
+        w->stage_bytes = bytes;
+    }
+    for (void *&q : w->copy_stream)
+        if (!q && (rc = cuda_check_step(cudaStreamCreateWithFlags((cudaStream_t *)&q, cudaStreamNonBlocking),
+                                        "copy stream")))
+            return rc;
+    for (void *&e : w->stage_event)
+        if (!e && (rc = cuda_check_step(cudaEventCreateWithFlags((cudaEvent_t *)&e, cudaEventDisableTiming),
+                                        "copy event")))
+            return rc;
+    cudaStream_t s_in = (cudaStream_t)w->copy_stream[0], s_out = (cudaStream_t)w->copy_stream[1];
+    cudaEvent_t *ev = (cudaEvent_t *)w->stage_event;  // [0,1] copied in, [2,3] stepped, [4,5] copied out, [6] start
+    // the copies start after the work already queued on the caller's stream
+    rc = cuda_check_step(cudaEventRecord(ev[6], st), "event");
+    if (!rc) rc = cuda_check_step(cudaStreamWaitEvent(s_in, ev[6], 0), "event wait");
+    if (!rc) rc = cuda_check_step(cudaStreamWaitEvent(s_out, ev[6], 0), "event wait");
+    // state b uses buffers k = b mod 2: its copy in overlaps the step of b - 1 and the copy out
+    // of b - 2
+    for (int64_t b = 0; b < nbatch && !rc; ++b) {
+        const int k = (int)(b & 1);
+        void *din = w->d_stage[k], *dout = w->d_stage[2 + k];
+        if (b >= 2) rc = cuda_check_step(cudaStreamWaitEvent(s_in, ev[2 + k], 0), "event wait");
+        if (!rc) rc = cuda_check_step(cudaMemcpyAsync(din, f_in[b], bytes, cudaMemcpyHostToDevice, s_in), "copy in");
+        if (!rc) rc = cuda_check_step(cudaEventRecord(ev[k], s_in), "event");
+        if (!rc) rc = cuda_check_step(cudaStreamWaitEvent(st, ev[k], 0), "event wait");
+        if (!rc && b >= 2) rc = cuda_check_step(cudaStreamWaitEvent(st, ev[4 + k], 0), "event wait");
+        if (!rc) rc = launch_step(w, dtype, din, dout, nullptr, st);
+        if (!rc) rc = cuda_check_step(cudaEventRecord(ev[2 + k], st), "event");
+        if (!rc) rc = cuda_check_step(cudaStreamWaitEvent(s_out, ev[2 + k], 0), "event wait");
+        if (!rc) rc = cuda_check_step(cudaMemcpyAsync(f_out[b], dout, bytes, cudaMemcpyDeviceToHost, s_out), "copy out");
+        if (!rc) rc = cuda_check_step(cudaEventRecord(ev[4 + k], s_out), "event");
+    }
+    // every copy and step has finished when the call returns
+    cudaError_t e1 = cudaStreamSynchronize(s_in), e2 = cudaStreamSynchronize(s_out);
+    if (!rc) rc = cuda_check_step(e1, "copy in");
+    if (!rc) rc = cuda_check_step(e2, "copy out");
+    if (!rc) rc = cuda_check_step(cudaStreamSynchronize(st), "mlbm_step_host");
+    return rc;
+}
+
 int mlbm_moments(const mlbm_weights *w, const mlbm_params *params, int dtype, const void *f,
                  double *rho, double *ux, double *uy, void *stream) {
     set_error("");

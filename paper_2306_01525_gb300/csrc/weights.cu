@@ -406,6 +406,11 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_scratch);
     cudaFree(w->d_partials);
     cudaFree(w->d_params);
+    for (void *b : w->d_stage) cudaFree(b);
+    for (void *q : w->copy_stream)
+        if (q) cudaStreamDestroy((cudaStream_t)q);
+    for (void *e : w->stage_event)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
     delete w;
 }
 
