@@ -70,7 +70,7 @@ def _step_source_hash():
     import re
 
     h = hashlib.sha256()
-    for f in ("step.cu", "d2q9_device.cuh"):
+    for f in ("step.cu", "d2q9_device.cuh", "tile_interp.cuh"):
         with open(os.path.join(ROOT, "paper_2306_01525_gb300", "csrc", f)) as fh:
             src = fh.read()
         if f == "step.cu":  # the step kernel and its launch, not the other kernels of the file
@@ -350,6 +350,11 @@ def bench_adjoint(steps: int = 2000):
     r0 = torch.ones(n, dtype=torch.float64, device=dev, requires_grad=True)
     a0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
     b0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
+    # warm-up: a short rollout and its backward pass (first use of the kernels and of autograd)
+    rw, uw, vw = rollout(w, tt, gt, r0, a0, b0, 10, dtype=mlbm.F32)
+    ((uw * uw + vw * vw).sum() + rw.sum()).backward()
+    for p_ in (tt, gt, r0, a0, b0):
+        p_.grad = None
     torch.cuda.synchronize()
     torch.cuda.reset_peak_memory_stats()
     t0 = time.perf_counter()

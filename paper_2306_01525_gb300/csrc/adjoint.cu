@@ -20,6 +20,7 @@
 
 #include "d2q9_device.cuh"
 #include "mlbm_internal.h"
+#include "tile_interp.cuh"
 
 namespace mlbm {
 
@@ -66,72 +67,86 @@ __device__ __forceinline__ void feq_vjp(const T (&lam)[9], T rho, T ux, T uy, T 
 
 template <typename T>
 struct AdjArgs {
-    const SegDev *__restrict__ seg;
     const TileDev *__restrict__ tiles;
-    const int32_t *__restrict__ idx;
-    const double *__restrict__ w64;  // canonical [8][K][n] per segment
+    const int32_t *__restrict__ halo;
+    const uint32_t *__restrict__ lidx;
+    const T *__restrict__ wt;           // tile-layout shape vectors of the forward step
     const uint16_t *__restrict__ mask;
-    const T *__restrict__ fdir;
-    const double *__restrict__ params;
+    const T *__restrict__ fdir;         // [2][N]
+    const T *__restrict__ params;       // [nseg][4]: tau, g, rho0, 1/tau in T
     const T *__restrict__ s_prev;
     const T *__restrict__ lam_next;
     T *__restrict__ lam_prev;
-    T *__restrict__ mut;    // [8][N] scratch: bounce-back-transposed cotangent of fhat
-    T *__restrict__ selfc;  // [8][N] scratch: centre contribution (1 - sum_{j>=1} w) mut
+    T *__restrict__ mut;    // [N][8] node-major: bounce-back-transposed cotangent of fhat
+    T *__restrict__ selfc;  // [8][N]: centre-coefficient term of the transposed interpolation
     double *__restrict__ partials;  // [ntiles][2]
-    const int32_t *__restrict__ csr_ptr;
-    const int32_t *__restrict__ csr_ent;
+    const int64_t *__restrict__ slice;    // [ceil(N/32)+1] offsets of the sliced entry table
+    const int32_t *__restrict__ tsrc;     // per entry slot: stored position of the reading node (-1: none)
+    const T *__restrict__ tw;             // per entry slot [8]: its shape-vector values (0: none)
     int64_t N;
     int ntiles;
 };
 
-// Local part of the reverse step at every node: recompute fhat (difference-form interpolation of
-// s_prev as in the forward kernel, then bounce-back), apply the transposed collision Jacobian to
-// lam_next, then the transposed bounce-back; accumulate dL/dtau and dL/dg per tile.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
+// Local part of the reverse step, tile by tile like the forward step (B nodes per CTA, halo of
+// s_prev staged in shared memory): recompute fhat with the forward's own arithmetic, apply the
+// transposed collision Jacobian to lam_next, then the transposed bounce-back; write the
+// cotangents for the transposed interpolation and the per-tile sums of dL/dtau and dL/dg.
+template <typename T, int B>
+__global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
+    using VT = typename V<T>::type;
     constexpr bool kDev = std::is_same<T, float>::value;
-    __shared__ double sh[2 * kThreads];
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
+    __shared__ double red[2][B / 32];
     const int64_t N = a.N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
+        stage_halo<T>(a.halo + tile.h_off, tile.U, a.s_prev, N, sh);
+        __syncthreads();
         double dtau = 0.0, dg = 0.0;
-        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
+        const int b = threadIdx.x;
+        if (b < tile.count) {
             const int64_t p = tile.begin + b;
-            const SegDev &sd = a.seg[tile.seg];
-            const int64_t n = sd.n, il = p - sd.off, KN = (int64_t)sd.K * n;
-            const int K = sd.K;
-            T f[9], wsum[9];
+            // fhat as the forward step computes it; cc = centre coefficient of each direction
+            VT c[NV], acc[NV], ws[NV], w0[NV];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                f[k] = a.s_prev[(int64_t)k * N + p];
-                wsum[k] = T(0);
+            for (int q = 0; q < NV; ++q) {
+                c[q] = sh[b * NV + q];
+                vzero(acc[q]);
+                vzero(ws[q]);
             }
-            T acc[9];
+            const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+            const VT *__restrict__ wp;
+            if constexpr (!kDev) {
+                wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) acc[k] = T(0);
-            for (int j = 1; j < K; ++j) {
-                const int32_t nb = a.idx[sd.idx_off + (int64_t)j * n + il];
-                const double *wj = a.w64 + sd.w_off + (int64_t)j * n + il;
-#pragma unroll
-                for (int k = 1; k < 9; ++k) {
-                    const T wk = (T)wj[(int64_t)(k - 1) * KN];
-                    acc[k] = fma(wk, a.s_prev[(int64_t)k * N + nb] - f[k], acc[k]);
-                    wsum[k] += wk;
+                for (int q = 0; q < NV; ++q) {
+                    w0[q] = __ldcs(wp + (int64_t)q * B);
+                    vmul(acc[q], w0[q], c[q]);
                 }
-            }
-            if constexpr (kDev) {
-                // FP32 forward: difference form, centre coefficient 1 - sum_{j>=1} w
-#pragma unroll
-                for (int k = 1; k < 9; ++k) f[k] += acc[k];
+                wp += (int64_t)NV * B;
             } else {
-                // FP64 forward: literal form, centre coefficient w_0
-                const double *w0 = a.w64 + sd.w_off + il;
+                wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+            }
+            interp_own<T, B, kDev>(wp, lp, sh, c, acc, ws, tile.K - 1);
+            T f[9], cc[9];
+            f[0] = a.s_prev[p];
+            cc[0] = T(1);
+            {
+                T cv[8], av[8], sv[8];
 #pragma unroll
-                for (int k = 1; k < 9; ++k) {
-                    const T c0 = (T)w0[(int64_t)(k - 1) * KN];
-                    f[k] = c0 * f[k] + (acc[k] + wsum[k] * f[k]);
-                    wsum[k] = T(1) - c0;
+                for (int q = 0; q < NV; ++q) {
+                    vunpack(cv + q * W, c[q]);
+                    vunpack(av + q * W, acc[q]);
+                    vunpack(sv + q * W, kDev ? ws[q] : w0[q]);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    f[k + 1] = kDev ? cv[k] + av[k] : av[k];
+                    cc[k + 1] = kDev ? T(1) - sv[k] : sv[k];
                 }
             }
             const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
@@ -143,9 +158,9 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                 for (int k = 1; k < 9; ++k)
                     if (mb >> k & 1u) f[k] = g[opp_of(k)];
             }
-            const double *pr = a.params + 4 * tile.seg;
-            const T tau = T(pr[0]), inv_tau = T(pr[3]);
-            const T rho_ref = kDev ? T(pr[2]) : T(0);
+            const T *pr = a.params + 4 * tile.seg;
+            const T inv_tau = pr[3];
+            const T rho_ref = kDev ? pr[2] : T(0);
             T drho, rho, ux, uy;
             moments_of<T>(f, rho_ref, drho, rho, ux, uy);
             const T usq15 = T(1.5) * (ux * ux + uy * uy);
@@ -160,8 +175,8 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                 st += lam[k] * (f[k] - geq);
                 sg += lam[k] * omega_of<T>(k) * T(3) * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
             }
-            dtau += (double)st / ((double)tau * (double)tau);
-            dg += (double)sg;
+            dtau = (double)(st * inv_tau * inv_tau);
+            dg = (double)sg;
             T Ar, Ax, Ay;
             feq_vjp<T>(lam, rho, ux, uy, Ar, Ax, Ay);
             const T ir = T(1) / rho;
@@ -179,45 +194,127 @@ __global__ void __launch_bounds__(kThreads) adj_local_kernel(AdjArgs<T> a) {
                 mt[l] = v;
             }
             a.lam_prev[p] = mt[0];
+            VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
 #pragma unroll
-            for (int k = 1; k < 9; ++k) {
-                a.mut[(int64_t)(k - 1) * N + p] = mt[k];
-                a.selfc[(int64_t)(k - 1) * N + p] = (T(1) - wsum[k]) * mt[k];
+            for (int q = 0; q < NV; ++q) {
+                VT v;
+                vpack(v, mt + 1 + q * W);
+                mo[q] = v;
             }
+#pragma unroll
+            for (int k = 1; k < 9; ++k) a.selfc[(int64_t)(k - 1) * N + p] = cc[k] * mt[k];
         }
-        block_sum2(dtau, dg, sh);
+        // per-tile sums in a fixed order: warps by shuffles, then the warps in index order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dtau += __shfl_xor_sync(0xffffffffu, dtau, o);
+            dg += __shfl_xor_sync(0xffffffffu, dg, o);
+        }
+        if (lane == 0) {
+            red[0][warp] = dtau;
+            red[1][warp] = dg;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
-            a.partials[2 * t] = dtau;
-            a.partials[2 * t + 1] = dg;
+            double s0 = 0.0, s1 = 0.0;
+            for (int q = 0; q < B / 32; ++q) {
+                s0 += red[0][q];
+                s1 += red[1][q];
+            }
+            a.partials[2 * t] = s0;
+            a.partials[2 * t + 1] = s1;
+        }
+        __syncthreads();
+    }
+}
+
+// lam_prev_k(m) = c_k(m) mut_k(m) + sum over the entries (i, j >= 1) of row m of the transposed
+// stencil (s_j(i) = m) of W_k[j](i) mut_k(i), k = 1..8: the transpose of the interpolation,
+// pulled in the row's fixed order.  The entries are tabulated sliced by 32 rows (a warp): entry
+// t of row 32 s + l sits at slice_off[s] + 32 t + l, rows padded to the slice's longest with
+// empty entries (src -1), so each warp reads 32 consecutive entries per pass (1 KB in FP32), and
+// mut is node-major (one 32-byte sector per gathered node in FP32).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
+    using VT = typename V<T>::type;
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;
+    const int64_t N = a.N;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < ((N + 31) & ~(int64_t)31);
+         m += (int64_t)gridDim.x * blockDim.x) {
+        const bool valid = m < N;
+        T acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = valid ? a.selfc[(int64_t)k * N + m] : T(0);
+        const int64_t s = m >> 5, b1 = a.slice[s + 1];
+        int64_t q = a.slice[s] + (m & 31);
+        auto add = [&](int32_t src, const VT (&w)[NV]) {
+            if (src < 0) return;
+            const VT *mi = reinterpret_cast<const VT *>(a.mut + (int64_t)src * 8);
+            T wv[8], mv[8];
+#pragma unroll
+            for (int qq = 0; qq < NV; ++qq) {
+                vunpack(wv + qq * W, w[qq]);
+                vunpack(mv + qq * W, __ldg(mi + qq));
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = fma(wv[k], mv[k], acc[k]);
+        };
+        for (; q + 32 < b1; q += 64) {
+            const int32_t s0 = __ldcs(a.tsrc + q), s1 = __ldcs(a.tsrc + q + 32);
+            VT w0[NV], w1[NV];
+#pragma unroll
+            for (int qq = 0; qq < NV; ++qq) {
+                w0[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + q * 8) + qq);
+                w1[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + (q + 32) * 8) + qq);
+            }
+            add(s0, w0);
+            add(s1, w1);
+        }
+        if (q < b1) {
+            VT w0[NV];
+#pragma unroll
+            for (int qq = 0; qq < NV; ++qq) w0[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + q * 8) + qq);
+            add(__ldcs(a.tsrc + q), w0);
+        }
+        if (valid) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = acc[k];
         }
     }
 }
 
-// lam_prev_k(m) = (1 - sum_{j>=1} W_k[j](m)) mut_k(m) + sum over (i, j >= 1) with s_j(i) = m of
-// W_k[j](i) mut_k(i), k = 1..8: the transpose of the difference-form interpolation.
+// Sliced table of the transposed stencil (layout above): row m's entry q = j n + i (member j of
+// node i, segment-local) gets the reading node's stored position and W_k[j](i), k = 1..8, in the
+// step's precision (the FP32 values round the FP64 shape vectors as the forward's FP32 layout
+// does); member-0 entries and padding get src -1 and zero weights.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
-    const int64_t N = a.N;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        const TileDev tile = a.tiles[t];
-        for (int b = threadIdx.x; b < tile.count; b += blockDim.x) {
-            const int64_t mnode = tile.begin + b;
-            const SegDev &sd = a.seg[tile.seg];
-            const int64_t n = sd.n, KN = (int64_t)sd.K * n;
-            T acc[8];
+__global__ void adj_table_kernel(int64_t N, const int32_t *__restrict__ node_seg, const SegDev *__restrict__ seg,
+                                 const double *__restrict__ w64c, const int32_t *__restrict__ csr_ptr,
+                                 const int32_t *__restrict__ csr_ent, const int64_t *__restrict__ slice,
+                                 int32_t *__restrict__ tsrc, T *__restrict__ tw) {
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
+        const SegDev sd = seg[node_seg[m]];
+        const int64_t s = m >> 5, base = slice[s] + (m & 31), len = (slice[s + 1] - slice[s]) >> 5;
+        const int32_t e0 = csr_ptr[m], e1 = csr_ptr[m + 1];
+        for (int64_t t = 0; t < len; ++t) {
+            const int64_t q = base + 32 * t;
+            int32_t src = -1;
+            T v[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = a.selfc[(int64_t)k * N + mnode];
-            const int32_t e0 = a.csr_ptr[mnode], e1 = a.csr_ptr[mnode + 1];
-            for (int32_t q = e0; q < e1; ++q) {
-                const int32_t ent = a.csr_ent[q];
-                if (ent < n) continue;  // member 0: the node itself, counted in selfc
-                const int64_t i = sd.off + (int64_t)(ent % n);
-                const double *wq = a.w64 + sd.w_off + ent;
+            for (int k = 0; k < 8; ++k) v[k] = T(0);
+            if (e0 + t < e1) {
+                const int64_t e = csr_ent[e0 + t];
+                const int64_t j = e / sd.n, i = e - j * sd.n;
+                if (j > 0) {
+                    src = (int32_t)(sd.off + i);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = fma((T)wq[(int64_t)k * KN], a.mut[(int64_t)k * N + i], acc[k]);
+                    for (int k = 0; k < 8; ++k) v[k] = (T)w64c[sd.w_off + ((int64_t)k * sd.K + j) * sd.n + i];
+                }
             }
+            tsrc[q] = src;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + mnode] = acc[k];
+            for (int k = 0; k < 8; ++k) tw[q * 8 + k] = v[k];
         }
     }
 }
@@ -336,28 +433,89 @@ int grid_of(const mlbm_weights *w, const void *fn) {
 }
 
 template <typename T>
+int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
+    const int i = std::is_same<T, float>::value ? 0 : 1;
+    if (w->d_adj_tw[i]) return MLBM_OK;
+    int rc = MLBM_OK;
+    if (!w->d_adj_slice) {
+        // slice offsets from the row lengths (host arithmetic on the downloaded row pointers)
+        std::vector<int32_t> ptr((size_t)w->N + 1);
+        if ((rc = cuda_check_step(cudaMemcpy(ptr.data(), w->d_csr_ptr, sizeof(int32_t) * ptr.size(),
+                                             cudaMemcpyDeviceToHost), "row pointers")))
+            return rc;
+        const int64_t ns = (w->N + 31) / 32;
+        std::vector<int64_t> off((size_t)ns + 1, 0);
+        for (int64_t s = 0; s < ns; ++s) {
+            int32_t len = 0;
+            for (int64_t m = 32 * s; m < std::min<int64_t>(32 * s + 32, w->N); ++m) len = std::max(len, ptr[m + 1] - ptr[m]);
+            off[s + 1] = off[s] + 32 * (int64_t)len;
+        }
+        w->adj_slots = off[ns];
+        if (cudaMalloc(&w->d_adj_slice, sizeof(int64_t) * off.size()) != cudaSuccess ||
+            cudaMalloc(&w->d_adj_tsrc, sizeof(int32_t) * std::max<int64_t>(1, w->adj_slots)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MLBM_ENOMEM, "adjoint table allocation failed");
+        }
+        if ((rc = cuda_check_step(cudaMemcpy(w->d_adj_slice, off.data(), sizeof(int64_t) * off.size(),
+                                             cudaMemcpyHostToDevice), "slice offsets")))
+            return rc;
+    }
+    if (cudaMalloc(&w->d_adj_tw[i], sizeof(T) * 8 * std::max<int64_t>(1, w->adj_slots)) != cudaSuccess) {
+        cudaGetLastError();
+        w->d_adj_tw[i] = nullptr;
+        return fail(MLBM_ENOMEM, "adjoint table allocation failed");
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + 255) / 256, 65536));
+    adj_table_kernel<T><<<grid, 256, 0, st>>>(w->N, w->d_node_seg, w->d_seg, w->d_w64, w->d_csr_ptr, w->d_csr_ent,
+                                              w->d_adj_slice, w->d_adj_tsrc, (T *)w->d_adj_tw[i]);
+    return cuda_check_step(cudaGetLastError(), "adjoint table launch");
+}
+
+template <typename T, int B>
+int launch_adj_local(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
+    const size_t smem = (size_t)w->umax * 8 * sizeof(T);
+    const void *fn = (const void *)adj_local_kernel<T, B>;
+    int rc = cuda_check_step(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                             "adjoint shared memory");
+    if (rc) return rc;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, smem);
+    if (per_sm < 1) return fail(MLBM_EINVAL, "a tile's halo does not fit in shared memory for the adjoint");
+    const int grid = std::max(1, std::min(w->ntiles, per_sm * w->num_sms));
+    adj_local_kernel<T, B><<<grid, B, smem, st>>>(a);
+    return MLBM_OK;
+}
+
+template <typename T>
 int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *lam_next, void *lam_prev, double *grad,
                    cudaStream_t st) {
+    constexpr bool kDev = std::is_same<T, float>::value;
+    int rc = ensure_adj_tables<T>(w, st);
+    if (rc) return rc;
     AdjArgs<T> a;
-    a.seg = w->d_seg;
     a.tiles = w->d_tiles;
-    a.idx = w->d_idx;
-    a.w64 = w->d_w64;
+    a.halo = w->d_halo;
+    a.lidx = w->d_lidx;
+    a.wt = kDev ? (const T *)w->d_w32t : (const T *)w->d_w64t;
     a.mask = w->has_mask ? w->d_mask : nullptr;
-    a.fdir = std::is_same<T, float>::value ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
-    a.params = w->d_params;
+    a.fdir = kDev ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
+    a.params = kDev ? (const T *)(w->d_params + 4 * (size_t)w->nseg) : (const T *)w->d_params;
     a.s_prev = (const T *)s_prev;
     a.lam_next = (const T *)lam_next;
     a.lam_prev = (T *)lam_prev;
     a.mut = (T *)w->d_scratch;
     a.selfc = (T *)w->d_scratch + 8 * (size_t)w->N;
     a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 16 * (size_t)w->N);
-    a.csr_ptr = w->d_csr_ptr;
-    a.csr_ent = w->d_csr_ent;
+    a.slice = w->d_adj_slice;
+    a.tsrc = w->d_adj_tsrc;
+    a.tw = (const T *)w->d_adj_tw[kDev ? 0 : 1];
     a.N = w->N;
     a.ntiles = w->ntiles;
-    adj_local_kernel<T><<<grid_of(w, (const void *)adj_local_kernel<T>), kThreads, 0, st>>>(a);
-    adj_transpose_kernel<T><<<grid_of(w, (const void *)adj_transpose_kernel<T>), kThreads, 0, st>>>(a);
+    rc = w->tile_nodes == kTileNodes ? launch_adj_local<T, kTileNodes>(w, a, st)
+                                     : launch_adj_local<T, kTileNodesSmall>(w, a, st);
+    if (rc) return rc;
+    const int tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + kThreads - 1) / kThreads, 8LL * w->num_sms));
+    adj_transpose_kernel<T><<<tgrid, kThreads, 0, st>>>(a);
     grad_finalize_kernel<<<w->nseg, kThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
     return cuda_check_step(cudaGetLastError(), "adjoint launch");
 }

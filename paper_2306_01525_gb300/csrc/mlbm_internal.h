@@ -137,6 +137,12 @@ struct mlbm_weights_impl {
     int64_t nsys = 0;
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
+    // adjoint: transposed-stencil entries sliced by 32 rows (slice offsets, then per entry slot
+    // the reading node and its shape-vector values in FP32 / FP64), tabulated on first use
+    int64_t *d_adj_slice = nullptr;
+    int64_t adj_slots = 0;
+    int32_t *d_adj_tsrc = nullptr;
+    void *d_adj_tw[2] = {nullptr, nullptr};
     // host-buffer steps (mlbm_step_host): two input and two output state buffers, one copy
     // stream per direction and their events, created on first use
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -18,6 +18,7 @@
 
 #include "d2q9_device.cuh"
 #include "mlbm_internal.h"
+#include "tile_interp.cuh"
 
 namespace mlbm {
 
@@ -43,67 +44,6 @@ struct StepArgs {
     int64_t N;
     int ntiles;
 };
-
-// Populations moved per shared-memory or shape-vector load: 4 directions in FP32 (16 B),
-// 2 directions in FP64 (16 B).
-template <typename T> struct V;
-template <> struct V<float> {
-    using type = float4;
-    static constexpr int width = 4;
-};
-template <> struct V<double> {
-    using type = double2;
-    static constexpr int width = 2;
-};
-
-// acc += w (x - c) (difference form, FP32) or acc += w x (literal form, FP64)
-template <bool kLiteral>
-__device__ __forceinline__ void vfma(float4 &acc, const float4 w, const float4 x, const float4 c) {
-    acc.x = fmaf(w.x, x.x - c.x, acc.x);
-    acc.y = fmaf(w.y, x.y - c.y, acc.y);
-    acc.z = fmaf(w.z, x.z - c.z, acc.z);
-    acc.w = fmaf(w.w, x.w - c.w, acc.w);
-}
-template <bool kLiteral>
-__device__ __forceinline__ void vfma(double2 &acc, const double2 w, const double2 x, const double2 c) {
-    if constexpr (kLiteral) {
-        acc.x = fma(w.x, x.x, acc.x);
-        acc.y = fma(w.y, x.y, acc.y);
-    } else {
-        acc.x = fma(w.x, x.x - c.x, acc.x);
-        acc.y = fma(w.y, x.y - c.y, acc.y);
-    }
-}
-__device__ __forceinline__ void vmul(float4 &acc, const float4 w, const float4 x) {
-    acc = make_float4(w.x * x.x, w.y * x.y, w.z * x.z, w.w * x.w);
-}
-__device__ __forceinline__ void vmul(double2 &acc, const double2 w, const double2 x) {
-    acc = make_double2(w.x * x.x, w.y * x.y);
-}
-__device__ __forceinline__ void vunpack(float *d, const float4 &a) {
-    d[0] = a.x;
-    d[1] = a.y;
-    d[2] = a.z;
-    d[3] = a.w;
-}
-__device__ __forceinline__ void vunpack(double *d, const double2 &a) {
-    d[0] = a.x;
-    d[1] = a.y;
-}
-__device__ __forceinline__ void vzero(float4 &v) { v = make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ void vzero(double2 &v) { v = make_double2(0.0, 0.0); }
-__device__ __forceinline__ void vpack(float4 &v, const float *s) { v = make_float4(s[0], s[1], s[2], s[3]); }
-__device__ __forceinline__ void vpack(double2 &v, const double *s) { v = make_double2(s[0], s[1]); }
-__device__ __forceinline__ void vunpack_sum(float *d, const float4 &c, const float4 &a) {
-    d[0] = c.x + a.x;
-    d[1] = c.y + a.y;
-    d[2] = c.z + a.z;
-    d[3] = c.w + a.w;
-}
-__device__ __forceinline__ void vunpack_sum(double *d, const double2 &c, const double2 &a) {
-    d[0] = c.x + a.x;
-    d[1] = c.y + a.y;
-}
 
 // Nearest-node stencils (Sec. 2.3, appendix algorithm): population k of node b is interpolated
 // in the stencil of its departure node L_k, so every direction has its own members; their halo
@@ -179,14 +119,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
         // 1. halo staging (own nodes first, then the other members sorted: mostly coalesced)
-        for (int u = threadIdx.x; u < tile.U; u += blockDim.x) {
-            const int64_t node = __ldg(a.halo + tile.h_off + u);
-            T v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = __ldg(a.fin + (int64_t)(k + 1) * N + node);
-#pragma unroll
-            for (int q = 0; q < NV; ++q) vpack(sh[u * NV + q], v + q * W);
-        }
+        stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
         __syncthreads();
         const int b = threadIdx.x;
         if (b < tile.count) {
@@ -196,55 +129,33 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
             if (tile.mode == MLBM_STENCIL_NEAREST) {
                 interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
             } else {
-            VT c[NV], acc[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                c[q] = sh[b * NV + q];
-                vzero(acc[q]);
-            }
-            const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
-            const VT *__restrict__ wp;
-            if constexpr (kLiteral) {
-                // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
-                wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
-#pragma unroll
-                for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
-                wp += (int64_t)NV * B;
-            } else {
-                wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
-            }
-            const int m1 = tile.K - 1;  // stencil members 1..K-1
-            int j = 0;
-            // 2. interpolation, two members per packed slot word
-#pragma unroll 2
-            for (; j + 1 < m1; j += 2) {
-                const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
-                VT w0[NV], w1[NV];
+                VT c[NV], acc[NV];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
-                    w0[q] = __ldcs(wp + (int64_t)(j * NV + q) * B);
-                    w1[q] = __ldcs(wp + (int64_t)((j + 1) * NV + q) * B);
+                    c[q] = sh[b * NV + q];
+                    vzero(acc[q]);
                 }
-                const int s0 = (int)(pr & 0xFFFFu), s1 = (int)(pr >> 16);
+                const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+                const VT *__restrict__ wp;
+                if constexpr (kLiteral) {
+                    // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
+                    wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma<kLiteral>(acc[q], w0[q], sh[s0 * NV + q], c[q]);
+                    for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
+                    wp += (int64_t)NV * B;
+                } else {
+                    wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+                }
+                // 2. interpolation over stencil members 1..K-1, two members per packed slot word
+                VT unused[NV];
+                interp_own<T, B, false>(wp, lp, sh, c, acc, unused, tile.K - 1);
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma<kLiteral>(acc[q], w1[q], sh[s1 * NV + q], c[q]);
-            }
-            if (j < m1) {
-                const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
-                const int s0 = (int)(pr & 0xFFFFu);
-#pragma unroll
-                for (int q = 0; q < NV; ++q)
-                    vfma<kLiteral>(acc[q], __ldcs(wp + (int64_t)(j * NV + q) * B), sh[s0 * NV + q], c[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                if constexpr (kLiteral)
-                    vunpack(f + 1 + q * W, acc[q]);
-                else
-                    vunpack_sum(f + 1 + q * W, c[q], acc[q]);
-            }
+                for (int q = 0; q < NV; ++q) {
+                    if constexpr (kLiteral)
+                        vunpack(f + 1 + q * W, acc[q]);
+                    else
+                        vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+                }
             }  // own-stencil interpolation
             // 3. wall bounce-back: unknown populations take the streamed opposite population
             if (a.mask) {

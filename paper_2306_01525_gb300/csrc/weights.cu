@@ -406,6 +406,9 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_scratch);
     cudaFree(w->d_partials);
     cudaFree(w->d_params);
+    cudaFree(w->d_adj_slice);
+    cudaFree(w->d_adj_tsrc);
+    for (void *b : w->d_adj_tw) cudaFree(b);
     for (void *b : w->d_stage) cudaFree(b);
     for (void *q : w->copy_stream)
         if (q) cudaStreamDestroy((cudaStream_t)q);

@@ -221,3 +221,55 @@ def test_rollout_gradient_matches_central_differences_20k():
     fdg = (loss(tau, g + 1e-8) - loss(tau, g - 1e-8)) / 2e-8
     assert gtau == pytest.approx(fdt, rel=1e-4)
     assert gg == pytest.approx(fdg, rel=1e-4)
+
+
+def test_fp32_adjoint_step_close_to_fp64_and_deterministic():
+    """The FP32 reverse step (transpose of the difference-form FP32 forward) agrees with the FP64
+    reverse step to FP32 accuracy, and repeats bit for bit."""
+    xy, dx, cloud, w, _, _ = _annulus(upload=False)
+    params = [(0.9, 2e-5, 1.0)]
+    n = xy.shape[1]
+    rng = np.random.default_rng(8)
+    fields = [_t(1 + 1e-3 * rng.standard_normal(n)), _t(3e-3 * rng.standard_normal(n)),
+              _t(3e-3 * rng.standard_normal(n))]
+    pert = _t(1e-4 * rng.standard_normal(9 * w.n))
+    lam = _t(rng.standard_normal(9 * w.n))
+    out = {}
+    for dt, td in ((mlbm.F64, torch.float64), (mlbm.F32, torch.float32)):
+        # the same physical state in each storage form (FP32: deviations from omega_k rho0)
+        s = torch.empty(9 * w.n, dtype=td, device=DEV)
+        mlbm.init(w, params, dt, *fields, s)
+        s += pert.to(td)
+        lp = torch.empty(9 * w.n, dtype=td, device=DEV)
+        g = torch.zeros(2, dtype=torch.float64, device=DEV)
+        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp, g)
+        out[dt] = (lp.double(), g.clone())
+        lp2 = torch.empty_like(lp)
+        g2 = torch.zeros(2, dtype=torch.float64, device=DEV)
+        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp2, g2)
+        assert torch.equal(lp, lp2) and torch.equal(g, g2)
+    a, b = out[mlbm.F64][0], out[mlbm.F32][0]
+    assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < 1e-5
+    np.testing.assert_allclose(out[mlbm.F32][1].cpu().numpy(), out[mlbm.F64][1].cpu().numpy(), rtol=1e-4)
+
+
+def test_adjoint_step_large_tiles_matches_finite_differences():
+    """A cloud large enough for 512-node tiles (360k nodes): the tiled reverse step against
+    central differences of the forward."""
+    xy = mi.jittered_lattice(600, 0.3, seed=12)
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=12, degree=2, dx_ml=1.0 / 600))
+    w = mlbm.build_weights(cloud)
+    params = [(0.8, 1e-5, 1.0)]
+    s = _rand_state(w, params, xy, seed=13)
+    rng = np.random.default_rng(14)
+    lam = _t(rng.standard_normal(9 * w.n))
+    v = _t(rng.standard_normal(9 * w.n))
+    lam_prev = torch.empty_like(lam)
+    grad = torch.zeros(2, dtype=torch.float64, device=DEV)
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad)
+    eps = 1e-5
+    fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
+    assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
+    h = 1e-6
+    fdt = (torch.dot(lam, _step(w, [(0.8 + h, 1e-5, 1.0)], s)) - torch.dot(lam, _step(w, [(0.8 - h, 1e-5, 1.0)], s))) / (2 * h)
+    assert float(grad[0]) == pytest.approx(float(fdt), rel=1e-6)
