@@ -240,12 +240,10 @@ __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;
     const int64_t N = a.N;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < ((N + 31) & ~(int64_t)31);
-         m += (int64_t)gridDim.x * blockDim.x) {
-        const bool valid = m < N;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
         T acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = valid ? a.selfc[(int64_t)k * N + m] : T(0);
+        for (int k = 0; k < 8; ++k) acc[k] = a.selfc[(int64_t)k * N + m];
         const int64_t s = m >> 5, b1 = a.slice[s + 1];
         int64_t q = a.slice[s] + (m & 31);
         auto add = [&](int32_t src, const VT (&w)[NV]) {
@@ -277,10 +275,8 @@ __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
             for (int qq = 0; qq < NV; ++qq) w0[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + q * 8) + qq);
             add(__ldcs(a.tsrc + q), w0);
         }
-        if (valid) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = acc[k];
-        }
+        for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = acc[k];
     }
 }
 
@@ -293,10 +289,13 @@ __global__ void adj_table_kernel(int64_t N, const int32_t *__restrict__ node_seg
                                  const double *__restrict__ w64c, const int32_t *__restrict__ csr_ptr,
                                  const int32_t *__restrict__ csr_ent, const int64_t *__restrict__ slice,
                                  int32_t *__restrict__ tsrc, T *__restrict__ tw) {
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
-        const SegDev sd = seg[node_seg[m]];
+    // rows N .. 32 ceil(N/32) - 1 of the last slice do not exist: their slots are filled empty
+    const int64_t rows = (N + 31) & ~(int64_t)31;
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < rows; m += (int64_t)gridDim.x * blockDim.x) {
+        const bool row = m < N;
+        const SegDev sd = seg[node_seg[row ? m : 0]];
         const int64_t s = m >> 5, base = slice[s] + (m & 31), len = (slice[s + 1] - slice[s]) >> 5;
-        const int32_t e0 = csr_ptr[m], e1 = csr_ptr[m + 1];
+        const int32_t e0 = row ? csr_ptr[m] : 0, e1 = row ? csr_ptr[m + 1] : 0;
         for (int64_t t = 0; t < len; ++t) {
             const int64_t q = base + 32 * t;
             int32_t src = -1;
@@ -465,7 +464,7 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
         w->d_adj_tw[i] = nullptr;
         return fail(MLBM_ENOMEM, "adjoint table allocation failed");
     }
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + 255) / 256, 65536));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + 31 + 255) / 256, 65536));
     adj_table_kernel<T><<<grid, 256, 0, st>>>(w->N, w->d_node_seg, w->d_seg, w->d_w64, w->d_csr_ptr, w->d_csr_ent,
                                               w->d_adj_slice, w->d_adj_tsrc, (T *)w->d_adj_tw[i]);
     return cuda_check_step(cudaGetLastError(), "adjoint table launch");
