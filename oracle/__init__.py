@@ -15,6 +15,9 @@ norms the paper states:
 * ``speed_rel_error``    pointwise relative speed error, eq. (vmag_error)
 * ``residual``           relative velocity residual used as the steady-state stop, Sec. 3
 
+and the Shan-Chen multiphase extension the paper's discussion names (``sc_psi``, ``sc_force``,
+``ScStepper``, ``sc_lattice_step``; model of Shan & Chen 1993, readings as in the library).
+
 Each function is checked against the paper and the mathematics in tests/test_oracle_pins.py.
 """
 from __future__ import annotations
@@ -85,6 +88,11 @@ def lib():
             L.orc_collide_field.argtypes = [i64, vp, vp, d, vp, vp]
             L.orc_moments_field.argtypes = [i64, vp, vp, vp, vp]
             L.orc_lattice_step.argtypes = [i32, i32, d, vp, vp, vp]
+            L.orc_sc_psi.restype = d
+            L.orc_sc_psi.argtypes = [d, d]
+            L.orc_sc_force.argtypes = [i64, i32, vp, vp, vp, d, vp, vp]
+            L.orc_sc_step.argtypes = [i64, i32, vp, vp, vp, vp, d, d, d, vp, vp, vp]
+            L.orc_sc_lattice_step.argtypes = [i32, i32, d, d, d, vp, vp, vp]
             L.orc_num_threads.restype = i32
             L.orc_set_threads.argtypes = [i32]
             _lib = L
@@ -288,6 +296,54 @@ def lattice_step(f, nx: int, ny: int, tau: float):
     out = np.zeros_like(f)
     scratch = np.zeros_like(f)
     lib().orc_lattice_step(nx, ny, tau, _p(f), _p(out), _p(scratch))
+    return out
+
+
+# ----------------------------------------------------------------------------- Shan-Chen
+
+def sc_psi(rho, rho0: float = 1.0):
+    """Shan-Chen pseudopotential psi(rho) = rho0 (1 - exp(-rho / rho0)) (Shan & Chen 1993)."""
+    r = np.atleast_1d(_f64(rho))
+    out = np.array([lib().orc_sc_psi(float(v), float(rho0)) for v in r])
+    return out if np.ndim(rho) else float(out[0])
+
+
+def sc_force(sidx, W, psi, G: float):
+    """Interaction force F_i = -G psi_i sum_k omega_k psi(x_i + e_k dx_ml) e_k, psi at
+    x_i + e_k dx_ml interpolated with the shape vector of the opposite direction."""
+    sidx = np.ascontiguousarray(sidx, np.int64)
+    W = _f64(W)
+    K, n = W.shape[1], W.shape[2]
+    fx, fy = np.zeros(n), np.zeros(n)
+    lib().orc_sc_force(n, K, _p(sidx), _p(W), _p(_f64(psi)), float(G), _p(fx), _p(fy))
+    return fx, fy
+
+
+class ScStepper(Stepper):
+    """Shan-Chen steps on a cloud without walls: psi of the current density, interaction force,
+    then the collide-and-stream step with that force (plus an optional body force)."""
+
+    def __init__(self, sidx, W, tau: float, G: float, rho0: float = 1.0, force=None):
+        super().__init__(sidx, W, tau, mask=None, force=force)
+        self.G = float(G)
+        self.rho0 = float(rho0)
+        self._sc_scratch = np.zeros((Q + 3) * self.n)
+
+    def step(self, f):
+        f = _f64(f)
+        out = np.zeros_like(f)
+        lib().orc_sc_step(self.n, self.K, _p(self.sidx), _p(self.W), _p(self.gx), _p(self.gy),
+                          self.tau, self.G, self.rho0, _p(f), _p(out), _p(self._sc_scratch))
+        return out
+
+
+def sc_lattice_step(f, nx: int, ny: int, tau: float, G: float, rho0: float = 1.0):
+    """Shan-Chen step on a periodic nx x ny lattice: psi(x + e_k) at the neighbouring node,
+    index-shift streaming."""
+    f = _f64(f)
+    out = np.zeros_like(f)
+    scratch = np.zeros((Q + 3) * f.shape[1])
+    lib().orc_sc_lattice_step(nx, ny, float(tau), float(G), float(rho0), _p(f), _p(out), _p(scratch))
     return out
 
 

@@ -436,18 +436,12 @@ void orc_init_equilibrium(int64_t n, const double *rho, const double *ux, const 
  *   2. f_k(i) <- sum_j W[k][j][i] f_post_k(sidx[k][j][i]) for k = 0..8;
  *   3. where bit k of mask[i] is set, f_k(i) <- the streamed f_k'(i) of step 2.
  * f_in and f_out are [9][n] and must differ; scratch holds [9][n] doubles. */
-void orc_step(int64_t n, int K, const int64_t *sidx, const double *W, const uint16_t *mask,
-              const double *gx, const double *gy, double tau, const double *f_in,
-              double *f_out, double *scratch)
+/* STREAM (Sec. 2.3) with the wall bounce-back of Sec. 3: f_k(i) <- sum_j W[k][j][i]
+ * post_k(sidx[k][j][i]) for k = 0..8, then where bit k of mask[i] is set, f_k(i) <- the
+ * streamed f_k'(i). */
+static void orc_stream(int64_t n, int K, const int64_t *sidx, const double *W, const uint16_t *mask,
+                       const double *post, double *f_out)
 {
-    double *post = scratch;
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < n; ++i) {
-        double f[ORC_Q], fp[ORC_Q];
-        for (int k = 0; k < ORC_Q; ++k) f[k] = f_in[(int64_t)k * n + i];
-        orc_collide(f, tau, gx ? gx[i] : 0.0, gy ? gy[i] : 0.0, fp);
-        for (int k = 0; k < ORC_Q; ++k) post[(int64_t)k * n + i] = fp[k];
-    }
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double fs[ORC_Q];
@@ -465,6 +459,21 @@ void orc_step(int64_t n, int K, const int64_t *sidx, const double *W, const uint
             f_out[(int64_t)k * n + i] = v;
         }
     }
+}
+
+void orc_step(int64_t n, int K, const int64_t *sidx, const double *W, const uint16_t *mask,
+              const double *gx, const double *gy, double tau, const double *f_in,
+              double *f_out, double *scratch)
+{
+    double *post = scratch;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double f[ORC_Q], fp[ORC_Q];
+        for (int k = 0; k < ORC_Q; ++k) f[k] = f_in[(int64_t)k * n + i];
+        orc_collide(f, tau, gx ? gx[i] : 0.0, gy ? gy[i] : 0.0, fp);
+        for (int k = 0; k < ORC_Q; ++k) post[(int64_t)k * n + i] = fp[k];
+    }
+    orc_stream(n, K, sidx, W, mask, post, f_out);
 }
 
 /* Collision applied to a whole field, used to express an oracle state f (post-streaming)
@@ -504,6 +513,116 @@ void orc_lattice_step(int nx, int ny, double tau, const double *f_in, double *f_
                 int sy = ((iy - orc_ey[k]) % ny + ny) % ny;
                 f_out[(int64_t)k * n + (int64_t)iy * nx + ix] =
                     scratch[(int64_t)k * n + (int64_t)sy * nx + sx];
+            }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Shan-Chen single-component multiphase extension (named in the paper's discussion as a    */
+/* model whose interactions sit in the local collision; the model itself is Shan & Chen     */
+/* 1993).  The paper gives no formulas: the readings are those of the library.              */
+/* ------------------------------------------------------------------------------------ */
+
+/* Pseudopotential psi(rho) = rho0 (1 - exp(-rho / rho0)). */
+double orc_sc_psi(double rho, double rho0) { return rho0 * (1.0 - exp(-rho / rho0)); }
+
+/* Interaction force at every node, F_i = -G psi_i sum_{k=1..8} omega_k psi(x_i + e_k dx_ml) e_k.
+ * The point x_i + e_k dx_ml is the departure point of the opposite direction k', so psi there is
+ * interpolated with the stencil and shape vector of direction k' at node i (sidx, W as in
+ * orc_build_weights). */
+void orc_sc_force(int64_t n, int K, const int64_t *sidx, const double *W, const double *psi, double G,
+                  double *Fx, double *Fy)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double sx = 0.0, sy = 0.0;
+        for (int k = 1; k < ORC_Q; ++k) {
+            int kp = orc_opposite(k);
+            double pk = 0.0;
+            for (int j = 0; j < K; ++j) {
+                int64_t t = ((int64_t)kp * K + j) * n + i;
+                pk += W[t] * psi[sidx[t]];
+            }
+            sx += orc_omega(k) * pk * orc_ex[k];
+            sy += orc_omega(k) * pk * orc_ey[k];
+        }
+        Fx[i] = -G * psi[i] * sx;
+        Fy[i] = -G * psi[i] * sy;
+    }
+}
+
+/* Shan-Chen collision: BGK towards the equilibrium at the shifted velocity
+ * u_eq = u + tau F / rho (Shan & Chen 1993), plus the body-force term of orc_collide. */
+void orc_sc_collide(const double *f, double tau, double Fx, double Fy, double gx, double gy,
+                    double *fpost)
+{
+    double rho, ux, uy;
+    orc_moments(f, &rho, &ux, &uy);
+    double vx = ux + tau * Fx / rho, vy = uy + tau * Fy / rho;
+    for (int k = 0; k < ORC_Q; ++k) {
+        double eq = orc_feq(k, rho, vx, vy);
+        double force = orc_omega(k) * (orc_ex[k] * gx + orc_ey[k] * gy) / orc_cs2;
+        fpost[k] = f[k] - (f[k] - eq) / tau + force;
+    }
+}
+
+/* One Shan-Chen step on a cloud without walls: density of the current state at every node,
+ * psi, the interaction force, the Shan-Chen collision (with the body force gx, gy if given),
+ * then STREAM.  scratch holds [9][n] + 3 n doubles. */
+void orc_sc_step(int64_t n, int K, const int64_t *sidx, const double *W, const double *gx,
+                 const double *gy, double tau, double G, double rho0, const double *f_in,
+                 double *f_out, double *scratch)
+{
+    double *post = scratch, *psi = scratch + (int64_t)ORC_Q * n, *Fx = psi + n, *Fy = Fx + n;
+    for (int64_t i = 0; i < n; ++i) {
+        double fl[ORC_Q], rho, ux, uy;
+        for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+        orc_moments(fl, &rho, &ux, &uy);
+        psi[i] = orc_sc_psi(rho, rho0);
+    }
+    orc_sc_force(n, K, sidx, W, psi, G, Fx, Fy);
+    for (int64_t i = 0; i < n; ++i) {
+        double fl[ORC_Q], fp[ORC_Q];
+        for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+        orc_sc_collide(fl, tau, Fx[i], Fy[i], gx ? gx[i] : 0.0, gy ? gy[i] : 0.0, fp);
+        for (int k = 0; k < ORC_Q; ++k) post[(int64_t)k * n + i] = fp[k];
+    }
+    orc_stream(n, K, sidx, W, NULL, post, f_out);
+}
+
+/* The same step on a periodic nx x ny lattice with index shifts: psi(x + e_k) is the value at
+ * the neighbouring lattice node, streaming as orc_lattice_step.  scratch holds [9][n] + 3 n. */
+void orc_sc_lattice_step(int nx, int ny, double tau, double G, double rho0, const double *f_in,
+                         double *f_out, double *scratch)
+{
+    int64_t n = (int64_t)nx * ny;
+    double *post = scratch, *psi = scratch + (int64_t)ORC_Q * n;
+    for (int64_t i = 0; i < n; ++i) {
+        double fl[ORC_Q], rho, ux, uy;
+        for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+        orc_moments(fl, &rho, &ux, &uy);
+        psi[i] = orc_sc_psi(rho, rho0);
+    }
+    for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix) {
+            double sx = 0.0, sy = 0.0;
+            for (int k = 1; k < ORC_Q; ++k) {
+                int jx = ((ix + orc_ex[k]) % nx + nx) % nx;
+                int jy = ((iy + orc_ey[k]) % ny + ny) % ny;
+                double pk = psi[(int64_t)jy * nx + jx];
+                sx += orc_omega(k) * pk * orc_ex[k];
+                sy += orc_omega(k) * pk * orc_ey[k];
+            }
+            int64_t i = (int64_t)iy * nx + ix;
+            double fl[ORC_Q], fp[ORC_Q];
+            for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+            orc_sc_collide(fl, tau, -G * psi[i] * sx, -G * psi[i] * sy, 0.0, 0.0, fp);
+            for (int k = 0; k < ORC_Q; ++k) post[(int64_t)k * n + i] = fp[k];
+        }
+    for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix)
+            for (int k = 0; k < ORC_Q; ++k) {
+                int sxi = ((ix - orc_ex[k]) % nx + nx) % nx;
+                int syi = ((iy - orc_ey[k]) % ny + ny) % ny;
+                f_out[(int64_t)k * n + (int64_t)iy * nx + ix] = post[(int64_t)k * n + (int64_t)syi * nx + sxi];
             }
 }
 
