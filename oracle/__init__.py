@@ -93,6 +93,7 @@ def lib():
             L.orc_sc_force.argtypes = [i64, i32, vp, vp, vp, d, vp, vp]
             L.orc_sc_step.argtypes = [i64, i32, vp, vp, vp, vp, d, d, d, vp, vp, vp]
             L.orc_sc_lattice_step.argtypes = [i32, i32, d, d, d, vp, vp, vp]
+            L.orc_sc_collide_field.argtypes = [i64, i32, vp, vp, d, d, d, vp, vp, vp]
             L.orc_num_threads.restype = i32
             L.orc_set_threads.argtypes = [i32]
             _lib = L
@@ -335,6 +336,20 @@ class ScStepper(Stepper):
         lib().orc_sc_step(self.n, self.K, _p(self.sidx), _p(self.W), _p(self.gx), _p(self.gy),
                           self.tau, self.G, self.rho0, _p(f), _p(out), _p(self._sc_scratch))
         return out
+
+
+def sc_collide_field(f, sidx, W, tau: float, G: float, rho0: float = 1.0):
+    """Shan-Chen collision of a whole field (no streaming): the post-collision state of the
+    same level, the form in which the GPU library holds its state."""
+    f = _f64(f)
+    sidx = np.ascontiguousarray(sidx, np.int64)
+    W = _f64(W)
+    n = f.shape[1]
+    out = np.zeros_like(f)
+    scratch = np.zeros(3 * n)
+    lib().orc_sc_collide_field(n, W.shape[1], _p(sidx), _p(W), float(tau), float(G), float(rho0),
+                               _p(f), _p(out), _p(scratch))
+    return out
 
 
 def sc_lattice_step(f, nx: int, ny: int, tau: float, G: float, rho0: float = 1.0):

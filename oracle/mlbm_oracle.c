@@ -588,6 +588,28 @@ void orc_sc_step(int64_t n, int K, const int64_t *sidx, const double *W, const d
     orc_stream(n, K, sidx, W, NULL, post, f_out);
 }
 
+/* The Shan-Chen collision of a whole field (psi, interaction force, shifted-equilibrium BGK;
+ * no streaming): the post-collision state of the same time level, as orc_collide_field.
+ * scratch holds 3 n doubles. */
+void orc_sc_collide_field(int64_t n, int K, const int64_t *sidx, const double *W, double tau,
+                          double G, double rho0, const double *f_in, double *f_out, double *scratch)
+{
+    double *psi = scratch, *Fx = psi + n, *Fy = Fx + n;
+    for (int64_t i = 0; i < n; ++i) {
+        double fl[ORC_Q], rho, ux, uy;
+        for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+        orc_moments(fl, &rho, &ux, &uy);
+        psi[i] = orc_sc_psi(rho, rho0);
+    }
+    orc_sc_force(n, K, sidx, W, psi, G, Fx, Fy);
+    for (int64_t i = 0; i < n; ++i) {
+        double fl[ORC_Q], fp[ORC_Q];
+        for (int k = 0; k < ORC_Q; ++k) fl[k] = f_in[(int64_t)k * n + i];
+        orc_sc_collide(fl, tau, Fx[i], Fy[i], 0.0, 0.0, fp);
+        for (int k = 0; k < ORC_Q; ++k) f_out[(int64_t)k * n + i] = fp[k];
+    }
+}
+
 /* The same step on a periodic nx x ny lattice with index shifts: psi(x + e_k) is the value at
  * the neighbouring lattice node, streaming as orc_lattice_step.  scratch holds [9][n] + 3 n. */
 void orc_sc_lattice_step(int nx, int ny, double tau, double G, double rho0, const double *f_in,

@@ -142,3 +142,24 @@ def test_flat_interface_coexistence_densities(G):
     rho_l, rho_g = r[ix == nx // 2].mean(), r[ix == 0].mean()
     rg, rl = _mechanical_stability_coexistence(G)
     assert rho_l == pytest.approx(rl, rel=0.015) and rho_g == pytest.approx(rg, rel=0.015), (rho_l, rho_g, rl, rg)
+
+
+def test_field_collision_adds_the_force_to_the_momentum_and_keeps_the_mass():
+    """Velocity-shift BGK: the momentum of each node changes by exactly (rho u_eq - rho u) / tau
+    = F, its mass not at all; with G = 0 it is the plain collision."""
+    xy, dx, sidx, W = _periodic_cloud(n_side=12, K=9, deg=2)
+    n = xy.shape[1]
+    rng = np.random.default_rng(4)
+    f = oracle.init_equilibrium(np.log(2.0) * (1 + 0.05 * rng.standard_normal(n)),
+                                0.01 * rng.standard_normal(n), 0.01 * rng.standard_normal(n))
+    f = f + 1e-3 * rng.standard_normal(f.shape)
+    tau, G = 0.9, -5.0
+    post = oracle.sc_collide_field(f, sidx, W, tau, G)
+    rho, _, _ = oracle.moments_field(f)
+    fx, fy = oracle.sc_force(sidx, W, oracle.sc_psi(rho), G)
+    ex, ey, _ = oracle.d2q9()
+    d = post - f
+    np.testing.assert_allclose(d.sum(axis=0), 0.0, atol=1e-15)
+    np.testing.assert_allclose(ex @ d, fx, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(ey @ d, fy, rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(oracle.sc_collide_field(f, sidx, W, tau, 0.0), oracle.collide_field(f, tau))
