@@ -262,6 +262,36 @@ int mlbm_step_host(mlbm_weights *w, const mlbm_params *params, int dtype, int64_
                    const void *const *f_in, void *const *f_out, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * mlbm_sc_step -- one time step of the Shan-Chen single-component multiphase model on the
+ * meshless cloud (the extension the paper's discussion names: the particle interactions sit
+ * in the local collision; the model is Shan & Chen 1993, the paper gives no formulas):
+ *   1. streaming as mlbm_step: fhat_k(i) = sum_j W_k[j](i) f^post_k(s_j(i));
+ *   2. psi_i = rho_psi (1 - exp(-rho_i / rho_psi)) of the density of fhat;
+ *   3. F_i = -G psi_i sum_k omega_k psi(x_i + e_k dx_ml) e_k, psi at x_i + e_k dx_ml (the
+ *      departure point of the opposite direction) interpolated with the streaming's own
+ *      shape vectors;
+ *   4. BGK collision of fhat towards f^eq(rho, u + tau F / rho), plus the body force term of
+ *      mlbm_step.
+ *
+ *   w          weights of periodic segments with own stencils only (no walls, no
+ *              MLBM_STENCIL_NEAREST): MLBM_EINVAL otherwise.
+ *   params     host, nseg parameter sets as mlbm_step (tau, body force g, rho0).
+ *   sc         host, nseg pairs {G, rho_psi}: coupling (with rho_psi = 1, G < -4 separates
+ *              phases) and the density scale of psi (> 0).
+ *   dtype, f_in, f_out, moments, stream   as mlbm_step; moments are those of fhat (before
+ *              the velocity shift).
+ * Two launches per step (stream + psi, then force + collision); a psi scratch of N doubles is
+ * kept in the weights object.  Errors: MLBM_EINVAL, MLBM_ENOMEM, MLBM_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    double G;       /* interaction strength */
+    double rho_psi; /* density scale of the pseudopotential */
+} mlbm_sc_params;
+
+int mlbm_sc_step(mlbm_weights *w, const mlbm_params *params, const mlbm_sc_params *sc, int dtype,
+                 const void *f_in, void *f_out, void *moments, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * mlbm_moments -- macroscopic fields (eq. macro_var) of the time level whose post-collision
  * state is f: rho = sum f, rho u = sum f e - g (collision conserves rho and adds exactly the
  * body force g to rho u, so these are the post-streaming moments the paper reports).

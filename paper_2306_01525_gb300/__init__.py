@@ -12,6 +12,7 @@ Names follow the C ABI without the ``mlbm_`` prefix:
     init, step, run               initial state and the fused pull-stream-collide step
     moments, norms                macroscopic fields (eq. macro_var), eq. (L2norm) sums
     adjoint_step, moments_adjoint, init_adjoint   reverse mode of the above
+    sc_step                       Shan-Chen multiphase step (extension named in the discussion)
 """
 from __future__ import annotations
 
@@ -28,7 +29,7 @@ __all__ = [
     "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
     "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
-    "lattice_init", "lattice_step", "step_host",
+    "lattice_init", "lattice_step", "step_host", "sc_step",
 ]
 
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5
@@ -48,6 +49,10 @@ class SegmentDesc(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("tau", _c_d), ("g", _c_d), ("rho0", _c_d)]
+
+
+class ScParams(ctypes.Structure):
+    _fields_ = [("G", _c_d), ("rho_psi", _c_d)]
 
 
 class MLBMError(RuntimeError):
@@ -91,6 +96,7 @@ def lib():
             L.mlbm_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_run.argtypes = [_vp, _vp, _c_int, _vp, _vp, _c_i64, _vp]
             L.mlbm_step_host.argtypes = [_vp, _vp, _c_int, _c_i64, _vp, _vp, _vp]
+            L.mlbm_sc_step.argtypes = [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_moments.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_norms.argtypes = [_vp, _vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
             L.mlbm_norms_noalloc.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
@@ -312,6 +318,28 @@ def step(w: Weights, params, dtype, f_in, f_out, moments_out=None, stream=None):
     _check(lib().mlbm_step(w.handle, _params(params, w.nseg), dtype,
                            _state(w, dtype, f_in, "f_in"), _state(w, dtype, f_out, "f_out"),
                            mom, _stream(stream)))
+
+
+def _sc_params(sc, nseg):
+    if isinstance(sc, (tuple, list)) and sc and isinstance(sc[0], (int, float)):
+        sc = [sc]
+    if len(sc) != nseg:
+        raise ValueError(f"need {nseg} Shan-Chen parameter pairs, got {len(sc)}")
+    arr = (ScParams * nseg)()
+    for s, p in enumerate(sc):
+        g, rp = (p["G"], p.get("rho_psi", 1.0)) if isinstance(p, dict) else (p[0], p[1] if len(p) > 1 else 1.0)
+        arr[s] = ScParams(float(g), float(rp))
+    return arr
+
+
+def sc_step(w: Weights, params, sc, dtype, f_in, f_out, moments_out=None, stream=None):
+    """One Shan-Chen multiphase step (mlbm_sc_step): streaming, psi of the streamed density,
+    interaction force from psi interpolated at x + e_k dx_ml, collision towards the shifted
+    equilibrium.  sc: per segment (G, rho_psi)."""
+    mom = None if moments_out is None else _dev_ptr(moments_out, _torch_dtype(dtype), 3 * w.n, "moments")
+    _check(lib().mlbm_sc_step(w.handle, _params(params, w.nseg), _sc_params(sc, w.nseg), dtype,
+                              _state(w, dtype, f_in, "f_in"), _state(w, dtype, f_out, "f_out"), mom,
+                              _stream(stream)))
 
 
 def _host_state(w, dtype, t, name):

@@ -143,6 +143,10 @@ struct mlbm_weights_impl {
     int64_t adj_slots = 0;
     int32_t *d_adj_tsrc = nullptr;
     void *d_adj_tw[2] = {nullptr, nullptr};
+    // Shan-Chen steps: [nseg][2] (G, rho_psi) in FP64 then FP32, and the psi scratch [N]
+    double *d_sc = nullptr;
+    std::vector<double> sc_cache;
+    void *d_sc_psi = nullptr;
     // host-buffer steps (mlbm_step_host): two input and two output state buffers, one copy
     // stream per direction and their events, created on first use
     void *d_stage[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -406,6 +406,8 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_scratch);
     cudaFree(w->d_partials);
     cudaFree(w->d_params);
+    cudaFree(w->d_sc);
+    cudaFree(w->d_sc_psi);
     cudaFree(w->d_adj_slice);
     cudaFree(w->d_adj_tsrc);
     for (void *b : w->d_adj_tw) cudaFree(b);
