@@ -373,6 +373,57 @@ def bench_adjoint(steps: int = 2000):
             "peak_torch_mem_gb": torch.cuda.max_memory_allocated() / 1e9}
 
 
+def sc_bytes_per_node(K: int) -> int:
+    """Algorithmic bytes of one FP32 Shan-Chen node update: both passes read the shape vectors
+    and slot indices (as a plain step); pass 1 reads the nine populations and writes the
+    streamed ones and psi, pass 2 reads psi and the streamed populations and writes the new
+    ones."""
+    per_pass = 8 * (K - 1) * 4 + 4 * (K - 1)
+    return 2 * per_pass + (36 + 36 + 4) + (4 + 36 + 36)
+
+
+def bench_shan_chen(n_side: int = 2048, steps: int = 200, warmup: int = 5):
+    """Shan-Chen multiphase steps (two launches each) on the headline cloud: 2048^2 jittered,
+    N_L = 30, P_4, dx_ml = h, G = -5.5, FP32, from a noisy uniform state at rho = ln 2."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    K, deg = 30, 4
+    xy = mi.jittered_lattice(n_side, 0.3, seed=3)
+    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=1.0 / n_side)
+    w = mlbm.build_weights(mlbm.build_cloud(xy, seg, device=True))
+    N = w.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    rng = np.random.default_rng(9)
+    td = lambda x: torch.as_tensor(x, dtype=torch.float64, device=dev)
+    params, sc = [(1.0, 0.0, 1.0)], (-5.5, 1.0)
+    a = torch.empty(9 * N, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F32, td(np.log(2.0) * (1 + 0.01 * rng.standard_normal(N))), td(np.zeros(N)),
+              td(np.zeros(N)), a)
+    for _ in range(warmup):
+        mlbm.sc_step(w, params, sc, mlbm.F32, a, b)
+        a, b = b, a
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        mlbm.sc_step(w, params, sc, mlbm.F32, a, b)
+        a, b = b, a
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = _peaks()
+    gbs = sc_bytes_per_node(K) * N / (ms * 1e-3) / 1e9
+    return {"workload": f"shan_chen_{n_side}sq_k{K}_d{deg}", "nodes": N, "value": N / (ms * 1e-3) / 1e9,
+            "unit": UNIT, "ms_per_step": ms, "launches_per_step": 2, "steps": steps,
+            "algorithmic_bytes_per_node": sc_bytes_per_node(K), "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
+            "dtype": "f32", "G": sc[0]}
+
+
 def bench_lattice(n_side: int = 2048, steps: int = 200, warmup: int = 5):
     """Standard lattice LBM (index-shift streaming) on an n_side^2 periodic lattice, FP32: the
     paper's comparison method at the node count of the headline workload."""
@@ -662,6 +713,8 @@ def run_mlbm(args):
         torch.cuda.empty_cache()
         extras["lattice_lbm"] = bench_lattice()
         torch.cuda.empty_cache()
+        extras["shan_chen"] = bench_shan_chen()
+        torch.cuda.empty_cache()
         extras["paper_sweep"] = bench_paper_sweep("f64")
     line = {
         "metric": METRIC, "value": gnups32, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -709,7 +762,7 @@ def main():
                     help="stencil rule of the main workload (own-node or nearest-node)")
     ap.add_argument("--ratio", type=float, default=1.0, help="dx_ml / h of the main workload")
     ap.add_argument("--leg", default=None,
-                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "paper_sweep"],
+                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep"],
                     help="run only this extra measurement and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep, annulus and adjoint measurements")
@@ -724,6 +777,7 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         legs = {"batched": lambda: bench_batched(1000), "annulus": bench_annulus,
                 "adjoint": lambda: bench_adjoint(2000), "lattice_lbm": bench_lattice,
+                "shan_chen": bench_shan_chen,
                 "paper_sweep": lambda: bench_paper_sweep("f64")}
         print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
         return 0
