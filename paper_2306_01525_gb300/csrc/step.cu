@@ -49,6 +49,8 @@ struct StepArgs {
 // in the stencil of its departure node L_k, so every direction has its own members; their halo
 // slots are packed [ceil(K/2)][B][8], member 0 being L_k itself.  Same forms as the own-stencil
 // path: FP32 differences to the centre value f_k(L_k) (members 1..K-1), FP64 the literal sum.
+// The halo is staged direction-major, shs[k][U]: a warp reading direction k at scattered slots
+// then spreads over all banks instead of the four that [U][8] would leave it.
 template <typename T, int B>
 __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileDev &tile, int b,
                                                const T *__restrict__ shs, T (&f)[9]) {
@@ -56,7 +58,7 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;
-    const int K = tile.K, JP = (K + 1) / 2;
+    const int K = tile.K, JP = (K + 1) / 2, U = tile.U;
     // slot words of a node for one member pair: eight directions, two 16-byte loads
     const uint4 *__restrict__ lp = reinterpret_cast<const uint4 *>(a.lidx + tile.l_off) + 2 * b;
     const VT *__restrict__ wbase = reinterpret_cast<const VT *>(a.wt + (kLiteral ? tile.w64_off : tile.w_off)) + b;
@@ -71,7 +73,7 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
         load_pairs(0, pr);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            c[k] = shs[(int)(pr[k] & 0xFFFFu) * 8 + k];
+            c[k] = shs[k * U + (int)(pr[k] & 0xFFFFu)];
             acc[k] = T(0);
         }
     }
@@ -90,7 +92,7 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int sl = h ? (int)(pr[k] >> 16) : (int)(pr[k] & 0xFFFFu);
-                const T x = shs[sl * 8 + k];
+                const T x = shs[k * U + sl];
                 acc[k] = kLiteral ? fma(wk[k], x, acc[k]) : fma(wk[k], x - c[k], acc[k]);
             }
         }
@@ -119,7 +121,10 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
         // 1. halo staging (own nodes first, then the other members sorted: mostly coalesced)
-        stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
+        if (tile.mode == MLBM_STENCIL_NEAREST)
+            stage_halo_dirmajor<T>(a.halo + tile.h_off, tile.U, a.fin, N, reinterpret_cast<T *>(sh));
+        else
+            stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
         __syncthreads();
         const int b = threadIdx.x;
         if (b < tile.count) {

@@ -104,6 +104,17 @@ __device__ __forceinline__ void stage_halo(const int32_t *__restrict__ halo, int
     }
 }
 
+// The same halo staged direction-major, sh[k][U] (k = 0..7 for populations 1..8).
+template <typename T>
+__device__ __forceinline__ void stage_halo_dirmajor(const int32_t *__restrict__ halo, int U, const T *__restrict__ f,
+                                                    int64_t N, T *sh) {
+    for (int u = threadIdx.x; u < U; u += blockDim.x) {
+        const int64_t node = __ldg(halo + u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sh[k * U + u] = __ldg(f + (int64_t)(k + 1) * N + node);
+    }
+}
+
 // Members 1..m1 of node b's own stencil: acc += W (x - c) (FP32) or acc += W x (FP64), with wp
 // at the shape vectors of member 1 for node b and lp at its slot words.  kSum also adds the
 // weights up in ws (the centre coefficient of the FP32 form is 1 - sum_{j>=1} W).
