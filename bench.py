@@ -365,12 +365,60 @@ def bench_adjoint(steps: int = 2000):
     loss.backward()
     torch.cuda.synchronize()
     t_all = time.perf_counter() - t0
+    peak_mem = torch.cuda.max_memory_allocated() / 1e9
+    # one reverse step and one forward step on their own: CUDA events on the launching stream,
+    # L2 flushed (a 256 MB write) before every timed launch
+    params = [(tau, g, 1.0)]
+    s = torch.empty(9 * n, dtype=torch.float32, device=dev)
+    mlbm.init(w, params, mlbm.F32, r0.detach(), a0.detach(), b0.detach(), s)
+    sn = torch.empty_like(s)
+    for _ in range(20):
+        mlbm.step(w, params, mlbm.F32, s, sn)
+        s, sn = sn, s
+    mlbm.step(w, params, mlbm.F32, s, sn)
+    lam = torch.randn(9 * n, dtype=torch.float32, device=dev, generator=torch.Generator(dev).manual_seed(3))
+    lp = torch.empty_like(lam)
+    gacc = torch.zeros(2, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def kernel_us(fn, reps=30):
+        fn()
+        total = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / reps * 1e3
+
+    rev_us = kernel_us(lambda: mlbm.adjoint_step(w, params, mlbm.F32, s, lam, lp, gacc, s_next=sn))
+    rev_rc_us = kernel_us(lambda: mlbm.adjoint_step(w, params, mlbm.F32, s, lam, lp, gacc))
+    fwd_us = kernel_us(lambda: mlbm.step(w, params, mlbm.F32, s, sn))
+    K = 24
+    bpn = adjoint_bytes_per_node(K)
+    peak, _ = _peaks()
+    gbs = bpn * n / (rev_us * 1e-6) / 1e9
     return {"workload": "annulus_250k_k24_d3_adjoint", "nodes": n, "steps": steps, "dtype": "f32",
             "checkpoint_every": int(np.ceil(np.sqrt(steps))), "forward_s": t_fwd,
             "forward_backward_s": t_all, "loss": float(loss),
             "dloss_dtau": float(tt.grad), "dloss_dg": float(gt.grad),
             "dloss_du0_norm": float(a0.grad.norm()),
-            "peak_torch_mem_gb": torch.cuda.max_memory_allocated() / 1e9}
+            "peak_torch_mem_gb": peak_mem,
+            "reverse_step": {"us": rev_us, "us_recompute_route": rev_rc_us, "forward_step_us": fwd_us,
+                             "algorithmic_bytes_per_node": bpn, "achieved_gbs": gbs,
+                             "frac_of_hbm": gbs / peak, "l2": "flushed before each launch"}}
+
+
+def adjoint_bytes_per_node(K: int) -> int:
+    """Algorithmic bytes of one FP32 reverse step per node: the shape-vector entries of the 8
+    moving directions for the K - 1 members other than the centre, their int32 stencil indices,
+    the forward output and the incoming cotangent read once, the outgoing cotangent written
+    once (nine populations each)."""
+    return 8 * (K - 1) * 4 + 4 * (K - 1) + 3 * 9 * 4
 
 
 def sc_bytes_per_node(K: int) -> int:

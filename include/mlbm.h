@@ -370,12 +370,18 @@ int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const 
  * transpose, then the transpose of the interpolation done as a deterministic pull over the
  * transposed stencil) and adds dL/dtau and dL/dg of this step to grad (device, 2 * nseg
  * float64, [seg][tau, g]).  s_prev is the forward state s^n (device, [9][N] dtype).
- * lam_next and lam_prev: device [9][N] dtype, must not alias.  Segments must use
- * MLBM_STENCIL_OWN (else MLBM_EINVAL).
+ * s_next is optional (NULL allowed): the forward's output s^{n+1} = Step(s^n) with the same
+ * weights and params.  The Jacobian and dL/dtau need the moments and the non-equilibrium part
+ * of the interpolated populations fhat; with s_next they are taken from it (the collision
+ * keeps rho, adds g to rho u and scales fhat - f^eq by 1 - 1/tau), which skips re-reading the
+ * shape vectors; without it, or when |1 - 1/tau| < 1/16 in any segment (fhat is not
+ * recoverable near tau = 1), fhat is recomputed from s_prev.  Both routes agree to rounding.
+ * lam_next and lam_prev: device [9][N] dtype; lam_prev must alias neither lam_next nor s_next.
+ * Segments must use MLBM_STENCIL_OWN (else MLBM_EINVAL).
  * ------------------------------------------------------------------------------------- */
 int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtype,
-                      const void *s_prev, const void *lam_next, void *lam_prev, double *grad,
-                      void *stream);
+                      const void *s_prev, const void *s_next, const void *lam_next,
+                      void *lam_prev, double *grad, void *stream);
 
 /* Seed of the reverse sweep for a loss on the macroscopic fields of the level whose
  * post-collision state is f (the outputs of mlbm_moments): given drho, dux, duy (device,

@@ -102,7 +102,7 @@ def lib():
             L.mlbm_norms_noalloc.argtypes = [_vp, _vp, _vp, _vp, _c_i64, _vp, _vp]
             L.mlbm_lattice_init.argtypes = [_c_i64, _c_i64, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_lattice_step.argtypes = [_c_i64, _c_i64, _vp, _c_int, _vp, _vp, _vp, _vp]
-            L.mlbm_adjoint_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
+            L.mlbm_adjoint_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_moments_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_init_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                             _vp, _vp]
@@ -447,11 +447,16 @@ def lattice_step(nx: int, ny: int, params, dtype, f_in, f_out, moments_out=None,
 
 # ----------------------------------------------------------------------------- adjoint
 
-def adjoint_step(w: Weights, params, dtype, s_prev, lam_next, lam_prev, grad, stream=None):
+def adjoint_step(w: Weights, params, dtype, s_prev, lam_next, lam_prev, grad, stream=None,
+                 s_next=None):
+    """lam_prev = dL/ds^n from lam_next = dL/ds^{n+1}; adds dL/dtau, dL/dg to grad.  s_next,
+    the forward's output Step(s_prev), is optional: with it the library takes the interpolated
+    populations' moments from it instead of recomputing the interpolation."""
     import torch
 
     _check(lib().mlbm_adjoint_step(w.handle, _params(params, w.nseg), dtype,
                                    _state(w, dtype, s_prev, "s_prev"),
+                                   _state(w, dtype, s_next, "s_next") if s_next is not None else None,
                                    _state(w, dtype, lam_next, "lam_next"),
                                    _state(w, dtype, lam_prev, "lam_prev"),
                                    _dev_ptr(grad, torch.float64, 2 * w.nseg, "grad"),

@@ -58,6 +58,7 @@ class _Rollout(torch.autograd.Function):
         moments_adjoint(w, params, dtype, ctx.final, z(drho), z(dux), z(duy), lam, grad)
         lam_prev = torch.empty_like(lam)
         nseg = len(ctx.ckpts)
+        after = ctx.final  # the state that follows the segment being swept
         for c in reversed(range(nseg)):
             n0 = c * C
             n1 = min(T, n0 + C)
@@ -66,11 +67,15 @@ class _Rollout(torch.autograd.Function):
                 nxt = torch.empty_like(states[-1])
                 step(w, params, dtype, states[-1], nxt)
                 states.append(nxt)
+            states.append(after)
             for n in reversed(range(n0, n1)):
-                adjoint_step(w, params, dtype, states[n - n0], lam, lam_prev, grad)
+                adjoint_step(w, params, dtype, states[n - n0], lam, lam_prev, grad,
+                             s_next=states[n - n0 + 1])
                 lam, lam_prev = lam_prev, lam
+            after = states[0]
             ctx.ckpts[c] = None
             del states
+        ctx.final = None
         d0 = [torch.empty(w.n, dtype=torch.float64, device=dev) for _ in range(3)]
         init_adjoint(w, params, dtype, rho0.contiguous(), ux0.contiguous(), uy0.contiguous(), lam,
                      d0[0], d0[1], d0[2], grad)

@@ -9,12 +9,20 @@
 //   B  the wall bounce-back fhat_k = fhat_k' on unknown populations      (Sec. 3)
 //   C  the BGK collision with forcing                                    (eq. LBM_collision, Sec. 3)
 // Reverse: mu = J_C^T lam, mut = B^T mu, lam_prev = S^T mut.  S^T is done as a pull over the
-// transposed stencil (for node m, the pairs (i, j) with s_j(i) = m), in a fixed order, so the
-// result is deterministic without atomics.  Parameter gradients are reduced per tile and then
-// per segment in a fixed order.
+// transposed stencil (for node m, the pairs (i, j) with s_j(i) = m, the centre pair (m, 0)
+// included), in a fixed order, so the result is deterministic without atomics.  Parameter
+// gradients are reduced per tile and then per segment in a fixed order.
+//
+// J_C and dL/dtau need the moments and the non-equilibrium part of fhat.  When the caller
+// passes the forward's output s' = C(fhat) they come from it: the collision keeps rho and adds
+// exactly g to rho u, and s' - F - s^eq = (1 - 1/tau)(fhat - s^eq), so no shape vector is read.
+// Near tau = 1 that division loses fhat (at tau = 1, s' = s^eq + F whatever fhat was), so with
+// |1 - 1/tau| < 1/16 in any segment, or without s', fhat is recomputed from s with the forward's
+// own tile interpolation.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <type_traits>
 
@@ -31,6 +39,9 @@ int cuda_check_step(cudaError_t e, const char *what);
 namespace {
 
 constexpr int kThreads = 256;
+// rows per CTA of the transposed pull: one row per thread, a CTA per 128 rows, so that the
+// hardware's block scheduling balances the rows' uneven lengths
+constexpr int kPullThreads = 128;
 
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
     sh[threadIdx.x] = a;
@@ -75,10 +86,10 @@ struct AdjArgs {
     const T *__restrict__ fdir;         // [2][N]
     const T *__restrict__ params;       // [nseg][4]: tau, g, rho0, 1/tau in T
     const T *__restrict__ s_prev;
+    const T *__restrict__ s_next;       // forward output C(fhat), or null (recompute fhat)
     const T *__restrict__ lam_next;
     T *__restrict__ lam_prev;
     T *__restrict__ mut;    // [N][8] node-major: bounce-back-transposed cotangent of fhat
-    T *__restrict__ selfc;  // [8][N]: centre-coefficient term of the transposed interpolation
     double *__restrict__ partials;  // [ntiles][2]
     const int64_t *__restrict__ slice;    // [ceil(N/32)+1] offsets of the sliced entry table
     const int32_t *__restrict__ tsrc;     // per entry slot: stored position of the reading node (-1: none)
@@ -87,10 +98,64 @@ struct AdjArgs {
     int ntiles;
 };
 
-// Local part of the reverse step, tile by tile like the forward step (B nodes per CTA, halo of
-// s_prev staged in shared memory): recompute fhat with the forward's own arithmetic, apply the
-// transposed collision Jacobian to lam_next, then the transposed bounce-back; write the
-// cotangents for the transposed interpolation and the per-tile sums of dL/dtau and dL/dg.
+// Transposed collision Jacobian (with d f^eq / d(rho, u)) and transposed bounce-back at node p:
+// mu = J_C^T lam at the moments (rho, u) of fhat, mut_l = [l not unknown] mu_l + [l' unknown]
+// mu_l'.  Writes lam_prev_0 = mut_0 (population 0 is not interpolated), returns mut_1..8.
+template <typename T>
+__device__ __forceinline__ void adj_collide_node(const AdjArgs<T> &a, int64_t p, const T (&lam)[9], T rho, T ux,
+                                                 T uy, T inv_tau, uint16_t mb, T (&out)[8]) {
+    T Ar, Ax, Ay;
+    feq_vjp<T>(lam, rho, ux, uy, Ar, Ax, Ay);
+    const T ir = T(1) / rho;
+    T mu[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l)
+        mu[l] = (T(1) - inv_tau) * lam[l] +
+                inv_tau * (Ar + (Ax * (T(ex_of(l)) - ux) + Ay * (T(ey_of(l)) - uy)) * ir);
+    T mt[9];
+#pragma unroll
+    for (int l = 0; l < 9; ++l) {
+        T v = (mb >> l & 1u) ? T(0) : mu[l];
+        if (l > 0 && (mb >> opp_of(l) & 1u)) v += mu[opp_of(l)];
+        mt[l] = v;
+    }
+    a.lam_prev[p] = mt[0];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] = mt[k + 1];
+}
+
+// Per-tile sums of the parameter-gradient terms in a fixed order: warps by shuffles, then the
+// warps in index order.  Called by every thread of the block; ends with a barrier.
+template <int B>
+__device__ __forceinline__ void tile_partials(double dtau, double dg, double (&red)[2][B / 32],
+                                              double *__restrict__ partials, int t) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dtau += __shfl_xor_sync(0xffffffffu, dtau, o);
+        dg += __shfl_xor_sync(0xffffffffu, dg, o);
+    }
+    if (lane == 0) {
+        red[0][warp] = dtau;
+        red[1][warp] = dg;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int q = 0; q < B / 32; ++q) {
+            s0 += red[0][q];
+            s1 += red[1][q];
+        }
+        partials[2 * t] = s0;
+        partials[2 * t + 1] = s1;
+    }
+    __syncthreads();
+}
+
+// Local part of the reverse step by recomputation, tile by tile like the forward step (B nodes
+// per CTA, halo of s_prev staged in shared memory): fhat with the forward's own arithmetic, then
+// the transposed collision and bounce-back; writes mut node-major for the scatter and the
+// per-tile sums of dL/dtau and dL/dg.
 template <typename T, int B>
 __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
     using VT = typename V<T>::type;
@@ -101,7 +166,6 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
     VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     __shared__ double red[2][B / 32];
     const int64_t N = a.N;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
         stage_halo<T>(a.halo + tile.h_off, tile.U, a.s_prev, N, sh);
@@ -110,44 +174,34 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
         const int b = threadIdx.x;
         if (b < tile.count) {
             const int64_t p = tile.begin + b;
-            // fhat as the forward step computes it; cc = centre coefficient of each direction
-            VT c[NV], acc[NV], ws[NV], w0[NV];
+            VT c[NV], acc[NV], ws[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 c[q] = sh[b * NV + q];
                 vzero(acc[q]);
-                vzero(ws[q]);
             }
             const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
             const VT *__restrict__ wp;
             if constexpr (!kDev) {
                 wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
 #pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    w0[q] = __ldcs(wp + (int64_t)q * B);
-                    vmul(acc[q], w0[q], c[q]);
-                }
+                for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
                 wp += (int64_t)NV * B;
             } else {
                 wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
             }
-            interp_own<T, B, kDev>(wp, lp, sh, c, acc, ws, tile.K - 1);
-            T f[9], cc[9];
+            interp_own<T, B, false>(wp, lp, sh, c, acc, ws, tile.K - 1);
+            T f[9];
             f[0] = a.s_prev[p];
-            cc[0] = T(1);
             {
-                T cv[8], av[8], sv[8];
+                T cv[8], av[8];
 #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     vunpack(cv + q * W, c[q]);
                     vunpack(av + q * W, acc[q]);
-                    vunpack(sv + q * W, kDev ? ws[q] : w0[q]);
                 }
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    f[k + 1] = kDev ? cv[k] + av[k] : av[k];
-                    cc[k + 1] = kDev ? T(1) - sv[k] : sv[k];
-                }
+                for (int k = 0; k < 8; ++k) f[k + 1] = kDev ? cv[k] + av[k] : av[k];
             }
             const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
             if (mb) {
@@ -177,65 +231,94 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
             }
             dtau = (double)(st * inv_tau * inv_tau);
             dg = (double)sg;
-            T Ar, Ax, Ay;
-            feq_vjp<T>(lam, rho, ux, uy, Ar, Ax, Ay);
-            const T ir = T(1) / rho;
-            T mu[9];
-#pragma unroll
-            for (int l = 0; l < 9; ++l)
-                mu[l] = (T(1) - inv_tau) * lam[l] +
-                        inv_tau * (Ar + (Ax * (T(ex_of(l)) - ux) + Ay * (T(ey_of(l)) - uy)) * ir);
-            // bounce-back transpose: mut_l = [l not unknown] mu_l + [l' unknown] mu_l'
-            T mt[9];
-#pragma unroll
-            for (int l = 0; l < 9; ++l) {
-                T v = (mb >> l & 1u) ? T(0) : mu[l];
-                if (l > 0 && (mb >> opp_of(l) & 1u)) v += mu[opp_of(l)];
-                mt[l] = v;
-            }
-            a.lam_prev[p] = mt[0];
+            T mt[8];
+            adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt);
             VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 VT v;
-                vpack(v, mt + 1 + q * W);
+                vpack(v, mt + q * W);
                 mo[q] = v;
             }
-#pragma unroll
-            for (int k = 1; k < 9; ++k) a.selfc[(int64_t)(k - 1) * N + p] = cc[k] * mt[k];
         }
-        // per-tile sums in a fixed order: warps by shuffles, then the warps in index order
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dtau += __shfl_xor_sync(0xffffffffu, dtau, o);
-            dg += __shfl_xor_sync(0xffffffffu, dg, o);
-        }
-        if (lane == 0) {
-            red[0][warp] = dtau;
-            red[1][warp] = dg;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int q = 0; q < B / 32; ++q) {
-                s0 += red[0][q];
-                s1 += red[1][q];
-            }
-            a.partials[2 * t] = s0;
-            a.partials[2 * t + 1] = s1;
-        }
-        __syncthreads();
+        tile_partials<B>(dtau, dg, red, a.partials, t);
     }
 }
 
-// lam_prev_k(m) = c_k(m) mut_k(m) + sum over the entries (i, j >= 1) of row m of the transposed
-// stencil (s_j(i) = m) of W_k[j](i) mut_k(i), k = 1..8: the transpose of the interpolation,
-// pulled in the row's fixed order.  The entries are tabulated sliced by 32 rows (a warp): entry
+// The same local part from the forward's output s_next = C(fhat), one node per thread and no
+// shape vector, halo or stencil read: rho is the moment of s_next, rho u that of s_next minus g
+// (the forcing term adds exactly g), and sum_k lam_k (fhat_k - s^eq_k) = sum_k lam_k (s_next_k
+// - F_k - s^eq_k) / (1 - 1/tau), with F_k = 3 omega_k e_k.g as the forward adds it.
+template <typename T, int B>
+__global__ void __launch_bounds__(B) adj_local_next_kernel(AdjArgs<T> a) {
+    using VT = typename V<T>::type;
+    constexpr bool kDev = std::is_same<T, float>::value;
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;
+    __shared__ double red[2][B / 32];
+    const int64_t N = a.N;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        const TileDev tile = a.tiles[t];
+        double dtau = 0.0, dg = 0.0;
+        const int b = threadIdx.x;
+        if (b < tile.count) {
+            const int64_t p = tile.begin + b;
+            const T *pr = a.params + 4 * tile.seg;
+            const T inv_tau = pr[3], gm = pr[1];
+            const T rho_ref = kDev ? pr[2] : T(0);
+            T s[9], lam[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                s[k] = __ldcs(a.s_next + (int64_t)k * N + p);
+                lam[k] = __ldcs(a.lam_next + (int64_t)k * N + p);
+            }
+            const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
+            const T fx = a.fdir[p], fy = a.fdir[N + p];
+            T gx = T(0), gy = T(0);
+            if (gm != T(0)) {
+                gx = gm * fx;
+                gy = gm * fy;
+            }
+            T drho, rho, ux, uy;
+            moments_of<T>(s, rho_ref, drho, rho, ux, uy);
+            const T ir = T(1) / rho;
+            ux -= gx * ir;
+            uy -= gy * ir;
+            const T usq15 = T(1.5) * (ux * ux + uy * uy);
+            T st = T(0), sg = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const T w3 = omega_of<T>(k) * T(3);
+                const T force = w3 * (T(ex_of(k)) * gx + T(ey_of(k)) * gy);
+                st += lam[k] * ((s[k] - force) - geq_of<T>(k, drho, rho, ux, uy, usq15));
+                sg += lam[k] * w3 * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
+            }
+            dtau = (double)(st * (inv_tau * inv_tau / (T(1) - inv_tau)));
+            dg = (double)sg;
+            T mt[8];
+            adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt);
+            VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                VT v;
+                vpack(v, mt + q * W);
+                mo[q] = v;
+            }
+        }
+        tile_partials<B>(dtau, dg, red, a.partials, t);
+    }
+}
+
+// lam_prev_k(m) = sum over the entries (i, j) of row m of the transposed stencil (s_j(i) = m) of
+// c_kj(i) mut_k(i), k = 1..8: the transpose of the interpolation, pulled in the row's fixed order
+// (j-major, so the centre entry (m, 0) comes first).  c_kj is the coefficient of s_k(s_j(i)) in
+// the forward's fhat_k(i): W_k[j](i), except the centre of the FP32 difference form,
+// 1 - sum_{j>=1} W_k[j](i).  The entries are tabulated sliced by 32 rows (a warp): entry
 // t of row 32 s + l sits at slice_off[s] + 32 t + l, rows padded to the slice's longest with
 // empty entries (src -1), so each warp reads 32 consecutive entries per pass (1 KB in FP32), and
 // mut is node-major (one 32-byte sector per gathered node in FP32).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
+__global__ void __launch_bounds__(kPullThreads) adj_transpose_kernel(AdjArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;
@@ -243,9 +326,18 @@ __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
         T acc[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = a.selfc[(int64_t)k * N + m];
+        for (int k = 0; k < 8; ++k) acc[k] = T(0);
         const int64_t s = m >> 5, b1 = a.slice[s + 1];
         int64_t q = a.slice[s] + (m & 31);
+        // entries q and q + 32 (a pair) of the row; past its end: src -1
+        auto load = [&](int64_t e, int32_t &src, VT (&w)[NV]) {
+            src = -1;
+            if (e < b1) {
+                src = __ldcs(a.tsrc + e);
+#pragma unroll
+                for (int qq = 0; qq < NV; ++qq) w[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + e * 8) + qq);
+            }
+        };
         auto add = [&](int32_t src, const VT (&w)[NV]) {
             if (src < 0) return;
             const VT *mi = reinterpret_cast<const VT *>(a.mut + (int64_t)src * 8);
@@ -258,22 +350,26 @@ __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = fma(wv[k], mv[k], acc[k]);
         };
-        for (; q + 32 < b1; q += 64) {
-            const int32_t s0 = __ldcs(a.tsrc + q), s1 = __ldcs(a.tsrc + q + 32);
-            VT w0[NV], w1[NV];
-#pragma unroll
-            for (int qq = 0; qq < NV; ++qq) {
-                w0[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + q * 8) + qq);
-                w1[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + (q + 32) * 8) + qq);
-            }
+        // the next pair's table entries are in flight while the current pair's cotangents are
+        // gathered (the rows of a slice share one length, so the loop is uniform over the warp)
+        int32_t s0, s1;
+        VT w0[NV], w1[NV];
+        load(q, s0, w0);
+        load(q + 32, s1, w1);
+        for (; q < b1; q += 64) {
+            int32_t n0, n1;
+            VT v0[NV], v1[NV];
+            load(q + 64, n0, v0);
+            load(q + 96, n1, v1);
             add(s0, w0);
             add(s1, w1);
-        }
-        if (q < b1) {
-            VT w0[NV];
+            s0 = n0;
+            s1 = n1;
 #pragma unroll
-            for (int qq = 0; qq < NV; ++qq) w0[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + q * 8) + qq);
-            add(__ldcs(a.tsrc + q), w0);
+            for (int qq = 0; qq < NV; ++qq) {
+                w0[qq] = v0[qq];
+                w1[qq] = v1[qq];
+            }
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = acc[k];
@@ -281,14 +377,16 @@ __global__ void __launch_bounds__(kThreads) adj_transpose_kernel(AdjArgs<T> a) {
 }
 
 // Sliced table of the transposed stencil (layout above): row m's entry q = j n + i (member j of
-// node i, segment-local) gets the reading node's stored position and W_k[j](i), k = 1..8, in the
-// step's precision (the FP32 values round the FP64 shape vectors as the forward's FP32 layout
-// does); member-0 entries and padding get src -1 and zero weights.
+// node i, segment-local) gets the reading node's stored position and its coefficients c_kj(i),
+// k = 1..8, in the step's precision (the FP32 values round the FP64 shape vectors as the
+// forward's FP32 layout does, and the FP32 centre coefficient adds them up in member order as
+// the forward's interpolation does); padding gets src -1 and zero coefficients.
 template <typename T>
 __global__ void adj_table_kernel(int64_t N, const int32_t *__restrict__ node_seg, const SegDev *__restrict__ seg,
                                  const double *__restrict__ w64c, const int32_t *__restrict__ csr_ptr,
                                  const int32_t *__restrict__ csr_ent, const int64_t *__restrict__ slice,
                                  int32_t *__restrict__ tsrc, T *__restrict__ tw) {
+    constexpr bool kDev = std::is_same<T, float>::value;
     // rows N .. 32 ceil(N/32) - 1 of the last slice do not exist: their slots are filled empty
     const int64_t rows = (N + 31) & ~(int64_t)31;
     for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < rows; m += (int64_t)gridDim.x * blockDim.x) {
@@ -305,10 +403,17 @@ __global__ void adj_table_kernel(int64_t N, const int32_t *__restrict__ node_seg
             if (e0 + t < e1) {
                 const int64_t e = csr_ent[e0 + t];
                 const int64_t j = e / sd.n, i = e - j * sd.n;
-                if (j > 0) {
-                    src = (int32_t)(sd.off + i);
+                src = (int32_t)(sd.off + i);
+                const double *wk = w64c + sd.w_off + i;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) v[k] = (T)w64c[sd.w_off + ((int64_t)k * sd.K + j) * sd.n + i];
+                for (int k = 0; k < 8; ++k) {
+                    if (j > 0 || !kDev) {
+                        v[k] = (T)wk[((int64_t)k * sd.K + j) * sd.n];
+                    } else {
+                        float ws = 0.f;
+                        for (int jj = 1; jj < sd.K; ++jj) ws += (float)wk[((int64_t)k * sd.K + jj) * sd.n];
+                        v[k] = (T)(1.f - ws);
+                    }
                 }
             }
             tsrc[q] = src;
@@ -410,7 +515,7 @@ __global__ void __launch_bounds__(kThreads) init_adjoint_kernel(
 }
 
 int ensure_adj_scratch(mlbm_weights *w) {
-    size_t need = sizeof(double) * (16 * (size_t)w->N + 2 * (size_t)w->ntiles);
+    size_t need = sizeof(double) * (8 * (size_t)w->N + 2 * (size_t)w->ntiles);
     if (w->d_scratch && w->scratch_bytes >= need) return MLBM_OK;
     cudaFree(w->d_scratch);
     w->d_scratch = nullptr;
@@ -485,9 +590,19 @@ int launch_adj_local(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
     return MLBM_OK;
 }
 
+template <typename T, int B>
+int launch_adj_local_next(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
+    const void *fn = (const void *)adj_local_next_kernel<T, B>;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, 0);
+    const int grid = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
+    adj_local_next_kernel<T, B><<<grid, B, 0, st>>>(a);
+    return MLBM_OK;
+}
+
 template <typename T>
-int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *lam_next, void *lam_prev, double *grad,
-                   cudaStream_t st) {
+int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *s_next, const void *lam_next, void *lam_prev,
+                   double *grad, cudaStream_t st) {
     constexpr bool kDev = std::is_same<T, float>::value;
     int rc = ensure_adj_tables<T>(w, st);
     if (rc) return rc;
@@ -500,21 +615,25 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *lam_next, vo
     a.fdir = kDev ? (const T *)w->d_fdir32 : (const T *)w->d_fdir64;
     a.params = kDev ? (const T *)(w->d_params + 4 * (size_t)w->nseg) : (const T *)w->d_params;
     a.s_prev = (const T *)s_prev;
+    a.s_next = (const T *)s_next;
     a.lam_next = (const T *)lam_next;
     a.lam_prev = (T *)lam_prev;
     a.mut = (T *)w->d_scratch;
-    a.selfc = (T *)w->d_scratch + 8 * (size_t)w->N;
-    a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 16 * (size_t)w->N);
+    a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 8 * (size_t)w->N);
     a.slice = w->d_adj_slice;
     a.tsrc = w->d_adj_tsrc;
     a.tw = (const T *)w->d_adj_tw[kDev ? 0 : 1];
     a.N = w->N;
     a.ntiles = w->ntiles;
-    rc = w->tile_nodes == kTileNodes ? launch_adj_local<T, kTileNodes>(w, a, st)
-                                     : launch_adj_local<T, kTileNodesSmall>(w, a, st);
+    if (s_next)
+        rc = w->tile_nodes == kTileNodes ? launch_adj_local_next<T, kTileNodes>(w, a, st)
+                                         : launch_adj_local_next<T, kTileNodesSmall>(w, a, st);
+    else
+        rc = w->tile_nodes == kTileNodes ? launch_adj_local<T, kTileNodes>(w, a, st)
+                                         : launch_adj_local<T, kTileNodesSmall>(w, a, st);
     if (rc) return rc;
-    const int tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + kThreads - 1) / kThreads, 8LL * w->num_sms));
-    adj_transpose_kernel<T><<<tgrid, kThreads, 0, st>>>(a);
+    const int tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + kPullThreads - 1) / kPullThreads, INT32_MAX));
+    adj_transpose_kernel<T><<<tgrid, kPullThreads, 0, st>>>(a);
     grad_finalize_kernel<<<w->nseg, kThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
     return cuda_check_step(cudaGetLastError(), "adjoint launch");
 }
@@ -527,11 +646,12 @@ using namespace mlbm;
 extern "C" {
 
 int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtype,
-                      const void *s_prev, const void *lam_next, void *lam_prev, double *grad,
-                      void *stream) {
+                      const void *s_prev, const void *s_next, const void *lam_next, void *lam_prev,
+                      double *grad, void *stream) {
     set_error("");
-    if (!w || !s_prev || !lam_next || !lam_prev || !grad) return fail(MLBM_EINVAL, "NULL argument");
+    if (!w || !params || !s_prev || !lam_next || !lam_prev || !grad) return fail(MLBM_EINVAL, "NULL argument");
     if (lam_next == lam_prev) return fail(MLBM_EINVAL, "lam_next and lam_prev must not alias");
+    if (s_next == lam_prev) return fail(MLBM_EINVAL, "s_next and lam_prev must not alias");
     int rc = check_dtype(w, dtype);
     if (rc) return rc;
     if (w->any_nearest)
@@ -540,8 +660,11 @@ int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtyp
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = set_params(wm, params, st))) return rc;
     if ((rc = ensure_adj_scratch(wm))) return rc;
-    return dtype == MLBM_F32 ? adjoint_step_t<float>(wm, s_prev, lam_next, lam_prev, grad, st)
-                             : adjoint_step_t<double>(wm, s_prev, lam_next, lam_prev, grad, st);
+    // fhat from s_next only where 1 - 1/tau keeps it recoverable (see the top of this file)
+    for (int s = 0; s < w->nseg && s_next; ++s)
+        if (!(std::fabs(1.0 - 1.0 / params[s].tau) >= 1.0 / 16)) s_next = nullptr;
+    return dtype == MLBM_F32 ? adjoint_step_t<float>(wm, s_prev, s_next, lam_next, lam_prev, grad, st)
+                             : adjoint_step_t<double>(wm, s_prev, s_next, lam_next, lam_prev, grad, st);
 }
 
 int mlbm_moments_adjoint(const mlbm_weights *w, const mlbm_params *params, int dtype,
@@ -555,7 +678,7 @@ int mlbm_moments_adjoint(const mlbm_weights *w, const mlbm_params *params, int d
     int rc = set_params(wm, params, st);
     if (rc) return rc;
     if ((rc = ensure_adj_scratch(wm))) return rc;
-    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 16 * (size_t)w->N);
+    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 8 * (size_t)w->N);
     if (dtype == MLBM_F32)
         moments_adjoint_kernel<float><<<grid_of(w, (const void *)moments_adjoint_kernel<float>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params, (const float *)f, drho, dux, duy, (float *)lam,
@@ -580,7 +703,7 @@ int mlbm_init_adjoint(const mlbm_weights *w, const mlbm_params *params, int dtyp
     int rc = set_params(wm, params, st);
     if (rc) return rc;
     if ((rc = ensure_adj_scratch(wm))) return rc;
-    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 16 * (size_t)w->N);
+    double *partials = (double *)((char *)wm->d_scratch + sizeof(double) * 8 * (size_t)w->N);
     if (dtype == MLBM_F32)
         init_adjoint_kernel<float><<<grid_of(w, (const void *)init_adjoint_kernel<float>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, rho, ux, uy, (const float *)lam0, drho, dux, duy, partials,

@@ -46,7 +46,10 @@ def _step(w, params, s):
     return out
 
 
-def test_adjoint_step_matches_finite_differences():
+@pytest.mark.parametrize("from_next", [False, True], ids=["recompute", "from_next"])
+def test_adjoint_step_matches_finite_differences(from_next):
+    """Both routes of the reverse step (fhat recomputed by interpolation, or taken from the
+    forward's output) against central differences of the forward."""
     xy, dx, cloud, w, _, _ = _annulus()
     tau, g = 0.9, 2e-5
     params = [(tau, g, 1.0)]
@@ -56,7 +59,8 @@ def test_adjoint_step_matches_finite_differences():
     v = _t(rng.standard_normal(9 * w.n))
     lam_prev = torch.empty_like(lam)
     grad = torch.zeros(2, dtype=torch.float64, device=DEV)
-    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad)
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad,
+                      s_next=_step(w, params, s) if from_next else None)
     eps = 1e-5
     fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
     assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
@@ -223,7 +227,8 @@ def test_rollout_gradient_matches_central_differences_20k():
     assert gg == pytest.approx(fdg, rel=1e-4)
 
 
-def test_fp32_adjoint_step_close_to_fp64_and_deterministic():
+@pytest.mark.parametrize("from_next", [False, True], ids=["recompute", "from_next"])
+def test_fp32_adjoint_step_close_to_fp64_and_deterministic(from_next):
     """The FP32 reverse step (transpose of the difference-form FP32 forward) agrees with the FP64
     reverse step to FP32 accuracy, and repeats bit for bit."""
     xy, dx, cloud, w, _, _ = _annulus(upload=False)
@@ -240,20 +245,25 @@ def test_fp32_adjoint_step_close_to_fp64_and_deterministic():
         s = torch.empty(9 * w.n, dtype=td, device=DEV)
         mlbm.init(w, params, dt, *fields, s)
         s += pert.to(td)
+        sn = None
+        if from_next:
+            sn = torch.empty_like(s)
+            mlbm.step(w, params, dt, s, sn)
         lp = torch.empty(9 * w.n, dtype=td, device=DEV)
         g = torch.zeros(2, dtype=torch.float64, device=DEV)
-        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp, g)
+        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp, g, s_next=sn)
         out[dt] = (lp.double(), g.clone())
         lp2 = torch.empty_like(lp)
         g2 = torch.zeros(2, dtype=torch.float64, device=DEV)
-        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp2, g2)
+        mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp2, g2, s_next=sn)
         assert torch.equal(lp, lp2) and torch.equal(g, g2)
     a, b = out[mlbm.F64][0], out[mlbm.F32][0]
     assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < 1e-5
     np.testing.assert_allclose(out[mlbm.F32][1].cpu().numpy(), out[mlbm.F64][1].cpu().numpy(), rtol=1e-4)
 
 
-def test_adjoint_step_large_tiles_matches_finite_differences():
+@pytest.mark.parametrize("from_next", [False, True], ids=["recompute", "from_next"])
+def test_adjoint_step_large_tiles_matches_finite_differences(from_next):
     """A cloud large enough for 512-node tiles (360k nodes): the tiled reverse step against
     central differences of the forward."""
     xy = mi.jittered_lattice(600, 0.3, seed=12)
@@ -266,10 +276,47 @@ def test_adjoint_step_large_tiles_matches_finite_differences():
     v = _t(rng.standard_normal(9 * w.n))
     lam_prev = torch.empty_like(lam)
     grad = torch.zeros(2, dtype=torch.float64, device=DEV)
-    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad)
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad,
+                      s_next=_step(w, params, s) if from_next else None)
     eps = 1e-5
     fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
     assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
     h = 1e-6
     fdt = (torch.dot(lam, _step(w, [(0.8 + h, 1e-5, 1.0)], s)) - torch.dot(lam, _step(w, [(0.8 - h, 1e-5, 1.0)], s))) / (2 * h)
     assert float(grad[0]) == pytest.approx(float(fdt), rel=1e-6)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_adjoint_from_next_state_agrees_with_recompute(dtype):
+    """The reverse step that takes fhat's moments and non-equilibrium part from the forward's
+    output equals the one that recomputes fhat by interpolation, to rounding (FP64: 1e-11; FP32:
+    the non-equilibrium part is divided by 1 - 1/tau = -0.43, 1e-5); near tau = 1 the library
+    recomputes whatever it is given, so both calls give the same bits."""
+    xy, dx, cloud, w, _, _ = _annulus(upload=False)
+    dt, td = (mlbm.F64, torch.float64) if dtype == "f64" else (mlbm.F32, torch.float32)
+    n = xy.shape[1]
+    rng = np.random.default_rng(21)
+    fields = [_t(1 + 1e-3 * rng.standard_normal(n)), _t(3e-3 * rng.standard_normal(n)),
+              _t(3e-3 * rng.standard_normal(n))]
+    pert = _t(1e-4 * rng.standard_normal(9 * w.n)).to(td)
+    lam = _t(rng.standard_normal(9 * w.n)).to(td)
+    for tau, same_bits in ((0.7, False), (1.0, True), (1.05, True), (1.2, False)):
+        params = [(tau, 3e-5, 1.0)]
+        s = torch.empty(9 * w.n, dtype=td, device=DEV)
+        mlbm.init(w, params, dt, *fields, s)
+        s += pert
+        sn = torch.empty_like(s)
+        mlbm.step(w, params, dt, s, sn)
+        res = []
+        for nxt in (None, sn):
+            lp = torch.empty_like(s)
+            g = torch.zeros(2, dtype=torch.float64, device=DEV)
+            mlbm.adjoint_step(w, params, dt, s, lam, lp, g, s_next=nxt)
+            res.append((lp.double(), g.cpu().numpy()))
+        (a, ga), (b, gb) = res
+        if same_bits:
+            assert torch.equal(a, b) and np.array_equal(ga, gb)
+            continue
+        tol = 1e-11 if dtype == "f64" else 1e-5
+        assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < tol
+        np.testing.assert_allclose(gb, ga, rtol=tol if dtype == "f64" else 1e-4)
