@@ -124,11 +124,12 @@ __device__ __forceinline__ void adj_collide_node(const AdjArgs<T> &a, int64_t p,
     for (int k = 0; k < 8; ++k) out[k] = mt[k + 1];
 }
 
-// Per-tile sums of the parameter-gradient terms in a fixed order: warps by shuffles, then the
-// warps in index order.  Called by every thread of the block; ends with a barrier.
-template <int B>
-__device__ __forceinline__ void tile_partials(double dtau, double dg, double (&red)[2][B / 32],
-                                              double *__restrict__ partials, int t) {
+// Per-tile sums of the parameter-gradient terms in a fixed order: warps by shuffles in the
+// step's precision (FP64 operations are scarce on this part), then the warps' sums in FP64 in
+// index order.  Called by every thread of the block; ends with a barrier.
+template <typename T, int B>
+__device__ __forceinline__ void tile_partials(T dtau, T dg, double (&red)[2][B / 32], double *__restrict__ partials,
+                                              int t) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -136,8 +137,8 @@ __device__ __forceinline__ void tile_partials(double dtau, double dg, double (&r
         dg += __shfl_xor_sync(0xffffffffu, dg, o);
     }
     if (lane == 0) {
-        red[0][warp] = dtau;
-        red[1][warp] = dg;
+        red[0][warp] = (double)dtau;
+        red[1][warp] = (double)dg;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
         const TileDev tile = a.tiles[t];
         stage_halo<T>(a.halo + tile.h_off, tile.U, a.s_prev, N, sh);
         __syncthreads();
-        double dtau = 0.0, dg = 0.0;
+        T dtau = T(0), dg = T(0);
         const int b = threadIdx.x;
         if (b < tile.count) {
             const int64_t p = tile.begin + b;
@@ -229,8 +230,8 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
                 st += lam[k] * (f[k] - geq);
                 sg += lam[k] * omega_of<T>(k) * T(3) * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
             }
-            dtau = (double)(st * inv_tau * inv_tau);
-            dg = (double)sg;
+            dtau = st * inv_tau * inv_tau;
+            dg = sg;
             T mt[8];
             adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt);
             VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
                 mo[q] = v;
             }
         }
-        tile_partials<B>(dtau, dg, red, a.partials, t);
+        tile_partials<T, B>(dtau, dg, red, a.partials, t);
     }
 }
 
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(B) adj_local_next_kernel(AdjArgs<T> a) {
     const int64_t N = a.N;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
-        double dtau = 0.0, dg = 0.0;
+        T dtau = T(0), dg = T(0);
         const int b = threadIdx.x;
         if (b < tile.count) {
             const int64_t p = tile.begin + b;
@@ -293,8 +294,8 @@ __global__ void __launch_bounds__(B) adj_local_next_kernel(AdjArgs<T> a) {
                 st += lam[k] * ((s[k] - force) - geq_of<T>(k, drho, rho, ux, uy, usq15));
                 sg += lam[k] * w3 * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
             }
-            dtau = (double)(st * (inv_tau * inv_tau / (T(1) - inv_tau)));
-            dg = (double)sg;
+            dtau = st * (inv_tau * inv_tau / (T(1) - inv_tau));
+            dg = sg;
             T mt[8];
             adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt);
             VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(B) adj_local_next_kernel(AdjArgs<T> a) {
                 mo[q] = v;
             }
         }
-        tile_partials<B>(dtau, dg, red, a.partials, t);
+        tile_partials<T, B>(dtau, dg, red, a.partials, t);
     }
 }
 
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kPullThreads) adj_transpose_kernel(AdjArgs<T> 
         for (int k = 0; k < 8; ++k) acc[k] = T(0);
         const int64_t s = m >> 5, b1 = a.slice[s + 1];
         int64_t q = a.slice[s] + (m & 31);
-        // entries q and q + 32 (a pair) of the row; past its end: src -1
+        // entry e of the row; past its end: src -1
         auto load = [&](int64_t e, int32_t &src, VT (&w)[NV]) {
             src = -1;
             if (e < b1) {
