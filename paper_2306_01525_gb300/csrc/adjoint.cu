@@ -24,7 +24,9 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <thread>
 #include <type_traits>
+#include <vector>
 
 #include "d2q9_device.cuh"
 #include "mlbm_internal.h"
@@ -91,9 +93,15 @@ struct AdjArgs {
     T *__restrict__ lam_prev;
     T *__restrict__ mut;    // [N][8] node-major: bounce-back-transposed cotangent of fhat
     double *__restrict__ partials;  // [ntiles][2]
-    const int64_t *__restrict__ slice;    // [ceil(N/32)+1] offsets of the sliced entry table
-    const int32_t *__restrict__ tsrc;     // per entry slot: stored position of the reading node (-1: none)
-    const T *__restrict__ tw;             // per entry slot [8]: its shape-vector values (0: none)
+    // transposed interpolation, per forward tile (see ensure_adj_tables)
+    const uint16_t *__restrict__ rowp;    // [ntiles][B] the tile's rows, longest first
+    const int32_t *__restrict__ rhalo;    // reverse halos (stored positions)
+    const int64_t *__restrict__ roff;     // [ntiles] offset of the tile's reverse halo
+    const int32_t *__restrict__ rcnt;     // [ntiles] its size
+    const int64_t *__restrict__ sbeg;     // [ntiles][B/32] first entry of each 32-row slice
+    const int32_t *__restrict__ slen;     // [ntiles][B/32] entries per row of the slice
+    const uint16_t *__restrict__ slot;    // per entry: reverse-halo slot of the reading node
+    const T *__restrict__ coef;           // per entry [8]: its coefficients c_kj
     int64_t N;
     int ntiles;
 };
@@ -103,7 +111,7 @@ struct AdjArgs {
 // mu_l'.  Writes lam_prev_0 = mut_0 (population 0 is not interpolated), returns mut_1..8.
 template <typename T>
 __device__ __forceinline__ void adj_collide_node(const AdjArgs<T> &a, int64_t p, const T (&lam)[9], T rho, T ux,
-                                                 T uy, T inv_tau, uint16_t mb, T (&out)[8]) {
+                                                 T uy, T inv_tau, uint16_t mb, T (&out)[8], bool write0 = true) {
     T Ar, Ax, Ay;
     feq_vjp<T>(lam, rho, ux, uy, Ar, Ax, Ay);
     const T ir = T(1) / rho;
@@ -119,7 +127,7 @@ __device__ __forceinline__ void adj_collide_node(const AdjArgs<T> &a, int64_t p,
         if (l > 0 && (mb >> opp_of(l) & 1u)) v += mu[opp_of(l)];
         mt[l] = v;
     }
-    a.lam_prev[p] = mt[0];
+    if (write0) a.lam_prev[p] = mt[0];
 #pragma unroll
     for (int k = 0; k < 8; ++k) out[k] = mt[k + 1];
 }
@@ -246,200 +254,233 @@ __global__ void __launch_bounds__(B, 1) adj_local_kernel(AdjArgs<T> a) {
     }
 }
 
-// The same local part from the forward's output s_next = C(fhat), one node per thread and no
-// shape vector, halo or stencil read: rho is the moment of s_next, rho u that of s_next minus g
-// (the forcing term adds exactly g), and sum_k lam_k (fhat_k - s^eq_k) = sum_k lam_k (s_next_k
-// - F_k - s^eq_k) / (1 - 1/tau), with F_k = 3 omega_k e_k.g as the forward adds it.
-template <typename T, int B>
-__global__ void __launch_bounds__(B) adj_local_next_kernel(AdjArgs<T> a) {
-    using VT = typename V<T>::type;
+// The local part from the forward's output s_next = C(fhat) at node p, no shape vector, halo or
+// stencil read: rho is the moment of s_next, rho u that of s_next minus g (the forcing term adds
+// exactly g), and sum_k lam_k (fhat_k - s^eq_k) = sum_k lam_k (s_next_k - F_k - s^eq_k) / (1 -
+// 1/tau), with F_k = 3 omega_k e_k.g as the forward adds it.  Returns mut_1..8 in mt; with own,
+// also writes lam_prev_0 and adds the node's dL/dtau and dL/dg terms.
+template <typename T>
+__device__ __forceinline__ void local_from_next(const AdjArgs<T> &a, int64_t p, int seg, bool own, T (&mt)[8],
+                                                T &dtau, T &dg) {
     constexpr bool kDev = std::is_same<T, float>::value;
+    const int64_t N = a.N;
+    const T *pr = a.params + 4 * seg;
+    const T inv_tau = pr[3], gm = pr[1];
+    const T rho_ref = kDev ? pr[2] : T(0);
+    T s[9], lam[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        s[k] = a.s_next[(int64_t)k * N + p];
+        lam[k] = a.lam_next[(int64_t)k * N + p];
+    }
+    const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
+    const T fx = a.fdir[p], fy = a.fdir[N + p];
+    T gx = T(0), gy = T(0);
+    if (gm != T(0)) {
+        gx = gm * fx;
+        gy = gm * fy;
+    }
+    T drho, rho, ux, uy;
+    moments_of<T>(s, rho_ref, drho, rho, ux, uy);
+    const T ir = T(1) / rho;
+    ux -= gx * ir;
+    uy -= gy * ir;
+    if (own) {
+        const T usq15 = T(1.5) * (ux * ux + uy * uy);
+        T st = T(0), sg = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const T w3 = omega_of<T>(k) * T(3);
+            const T force = w3 * (T(ex_of(k)) * gx + T(ey_of(k)) * gy);
+            st += lam[k] * ((s[k] - force) - geq_of<T>(k, drho, rho, ux, uy, usq15));
+            sg += lam[k] * w3 * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
+        }
+        dtau += st * (inv_tau * inv_tau / (T(1) - inv_tau));
+        dg += sg;
+    }
+    adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt, own);
+}
+
+// acc += w * m component-wise
+__device__ __forceinline__ void vfma_acc(float4 &acc, const float4 w, const float4 m) {
+    acc.x = fmaf(w.x, m.x, acc.x);
+    acc.y = fmaf(w.y, m.y, acc.y);
+    acc.z = fmaf(w.z, m.z, acc.z);
+    acc.w = fmaf(w.w, m.w, acc.w);
+}
+__device__ __forceinline__ void vfma_acc(double2 &acc, const double2 w, const double2 m) {
+    acc.x = fma(w.x, m.x, acc.x);
+    acc.y = fma(w.y, m.y, acc.y);
+}
+
+// The transposed interpolation, tile by tile on the forward's tiles (B rows per CTA):
+//   1. the cotangents mut of the tile's reverse halo (its own nodes, then every other node whose
+//      stencil holds one of them) are staged in shared memory as [slot][8]: with kFromNext
+//      computed there from s_next and lam_next (own nodes also give lam_prev_0 and the
+//      parameter-gradient terms), otherwise read from the node-major buffer adj_local_kernel
+//      wrote;
+//   2. row m (thread b handles the tile's b-th longest row) sums c_kj(i) mut_k(i) over its
+//      entries (i, j), s_j(i) = m, in its fixed order (j-major: the centre entry (m, 0) first):
+//      lam_prev_k(m), k = 1..8.  c_kj is the coefficient of s_k(s_j(i)) in the forward's
+//      fhat_k(i): W_k[j](i), except the centre of the FP32 difference form, 1 - sum_{j>=1}
+//      W_k[j](i).  The entries are sliced by 32 rows (entry e of the slice's lane l at
+//      sbeg + 32 e + l, rows padded to the slice's longest with zero coefficients), so a warp
+//      streams 32 consecutive entries per pass, and the gathered cotangents come from shared
+//      memory.  No atomics: deterministic.
+template <typename T, int B, bool kFromNext>
+__global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
+    using VT = typename V<T>::type;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     __shared__ double red[2][B / 32];
     const int64_t N = a.N;
+    const int b = threadIdx.x;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
+        const int U = a.rcnt[t];
+        const int32_t *__restrict__ rh = a.rhalo + a.roff[t];
         T dtau = T(0), dg = T(0);
-        const int b = threadIdx.x;
-        if (b < tile.count) {
-            const int64_t p = tile.begin + b;
-            const T *pr = a.params + 4 * tile.seg;
-            const T inv_tau = pr[3], gm = pr[1];
-            const T rho_ref = kDev ? pr[2] : T(0);
-            T s[9], lam[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                s[k] = __ldcs(a.s_next + (int64_t)k * N + p);
-                lam[k] = __ldcs(a.lam_next + (int64_t)k * N + p);
-            }
-            const uint16_t mb = a.mask ? a.mask[p] : (uint16_t)0;
-            const T fx = a.fdir[p], fy = a.fdir[N + p];
-            T gx = T(0), gy = T(0);
-            if (gm != T(0)) {
-                gx = gm * fx;
-                gy = gm * fy;
-            }
-            T drho, rho, ux, uy;
-            moments_of<T>(s, rho_ref, drho, rho, ux, uy);
-            const T ir = T(1) / rho;
-            ux -= gx * ir;
-            uy -= gy * ir;
-            const T usq15 = T(1.5) * (ux * ux + uy * uy);
-            T st = T(0), sg = T(0);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const T w3 = omega_of<T>(k) * T(3);
-                const T force = w3 * (T(ex_of(k)) * gx + T(ey_of(k)) * gy);
-                st += lam[k] * ((s[k] - force) - geq_of<T>(k, drho, rho, ux, uy, usq15));
-                sg += lam[k] * w3 * (T(ex_of(k)) * fx + T(ey_of(k)) * fy);
-            }
-            dtau = st * (inv_tau * inv_tau / (T(1) - inv_tau));
-            dg = sg;
+        for (int u = b; u < U; u += B) {
+            const int64_t node = rh[u];
             T mt[8];
-            adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt);
-            VT *mo = reinterpret_cast<VT *>(a.mut + p * 8);
+            if constexpr (kFromNext) {
+                local_from_next<T>(a, node, tile.seg, u < tile.count, mt, dtau, dg);
+            } else {
+                const VT *mi = reinterpret_cast<const VT *>(a.mut + node * 8);
 #pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                VT v;
-                vpack(v, mt + q * W);
-                mo[q] = v;
+                for (int q = 0; q < NV; ++q) vunpack(mt + q * W, mi[q]);
             }
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vpack(sh[u * NV + q], mt + q * W);
         }
-        tile_partials<T, B>(dtau, dg, red, a.partials, t);
+        __syncthreads();
+        if (b < tile.count) {
+            const int64_t m = tile.begin + a.rowp[(int64_t)t * B + b];
+            const int ws = t * (B / 32) + (b >> 5);
+            const int L = a.slen[ws];
+            const int64_t q0 = a.sbeg[ws] + (b & 31);
+            const uint16_t *__restrict__ sp = a.slot + q0;
+            const VT *__restrict__ cp = reinterpret_cast<const VT *>(a.coef) + q0 * NV;
+            VT acc[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vzero(acc[q]);
+            // four entries per pass: their slots and coefficients are loaded before any is used
+            int e = 0;
+            for (; e + 3 < L; e += 4) {
+                int sl[4];
+                VT c[4][NV];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    sl[r] = sp[(int64_t)32 * (e + r)];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) c[r][q] = __ldcs(cp + ((int64_t)32 * (e + r)) * NV + q);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) vfma_acc(acc[q], c[r][q], sh[sl[r] * NV + q]);
+            }
+            for (; e < L; ++e) {
+                const int s0 = sp[(int64_t)32 * e];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vfma_acc(acc[q], __ldcs(cp + ((int64_t)32 * e) * NV + q), sh[s0 * NV + q]);
+            }
+            T v[8];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vunpack(v + q * W, acc[q]);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = v[k];
+        }
+        if constexpr (kFromNext)
+            tile_partials<T, B>(dtau, dg, red, a.partials, t);
+        else
+            __syncthreads();
     }
 }
 
-// lam_prev_k(m) = sum over the entries (i, j) of row m of the transposed stencil (s_j(i) = m) of
-// c_kj(i) mut_k(i), k = 1..8: the transpose of the interpolation, pulled in the row's fixed order
-// (j-major, so the centre entry (m, 0) comes first).  c_kj is the coefficient of s_k(s_j(i)) in
-// the forward's fhat_k(i): W_k[j](i), except the centre of the FP32 difference form,
-// 1 - sum_{j>=1} W_k[j](i).  The entries are tabulated sliced by 32 rows (a warp): entry
-// t of row 32 s + l sits at slice_off[s] + 32 t + l, rows padded to the slice's longest with
-// empty entries (src -1), so each warp reads 32 consecutive entries per pass (1 KB in FP32), and
-// mut is node-major (one 32-byte sector per gathered node in FP32).
+// Coefficients of the sliced entry table: thread (t, b) fills the entries of the tile's b-th
+// row (slice b / 32, lane b % 32): entry e of that row is csr entry csr_ptr[m] + e, q = j n + i
+// (member j of node i, segment-local), with coefficients c_kj(i), k = 1..8, in the step's
+// precision (the FP32 values round the FP64 shape vectors as the forward's FP32 layout does, and
+// the FP32 centre coefficient adds them up in member order as the forward's interpolation
+// does); entries past the row's end (padding) get zeros.
 template <typename T>
-__global__ void __launch_bounds__(kPullThreads) adj_transpose_kernel(AdjArgs<T> a) {
-    using VT = typename V<T>::type;
-    constexpr int W = V<T>::width;
-    constexpr int NV = 8 / W;
-    const int64_t N = a.N;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < N; m += (int64_t)gridDim.x * blockDim.x) {
-        T acc[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[k] = T(0);
-        const int64_t s = m >> 5, b1 = a.slice[s + 1];
-        int64_t q = a.slice[s] + (m & 31);
-        // entry e of the row; past its end: src -1
-        auto load = [&](int64_t e, int32_t &src, VT (&w)[NV]) {
-            src = -1;
-            if (e < b1) {
-                src = __ldcs(a.tsrc + e);
-#pragma unroll
-                for (int qq = 0; qq < NV; ++qq) w[qq] = __ldcs(reinterpret_cast<const VT *>(a.tw + e * 8) + qq);
-            }
-        };
-        auto add = [&](int32_t src, const VT (&w)[NV]) {
-            if (src < 0) return;
-            const VT *mi = reinterpret_cast<const VT *>(a.mut + (int64_t)src * 8);
-            T wv[8], mv[8];
-#pragma unroll
-            for (int qq = 0; qq < NV; ++qq) {
-                vunpack(wv + qq * W, w[qq]);
-                vunpack(mv + qq * W, __ldg(mi + qq));
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) acc[k] = fma(wv[k], mv[k], acc[k]);
-        };
-        // the next pair's table entries are in flight while the current pair's cotangents are
-        // gathered (the rows of a slice share one length, so the loop is uniform over the warp)
-        int32_t s0, s1;
-        VT w0[NV], w1[NV];
-        load(q, s0, w0);
-        load(q + 32, s1, w1);
-        for (; q < b1; q += 64) {
-            int32_t n0, n1;
-            VT v0[NV], v1[NV];
-            load(q + 64, n0, v0);
-            load(q + 96, n1, v1);
-            add(s0, w0);
-            add(s1, w1);
-            s0 = n0;
-            s1 = n1;
-#pragma unroll
-            for (int qq = 0; qq < NV; ++qq) {
-                w0[qq] = v0[qq];
-                w1[qq] = v1[qq];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) a.lam_prev[(int64_t)(k + 1) * N + m] = acc[k];
-    }
-}
-
-// Sliced table of the transposed stencil (layout above): row m's entry q = j n + i (member j of
-// node i, segment-local) gets the reading node's stored position and its coefficients c_kj(i),
-// k = 1..8, in the step's precision (the FP32 values round the FP64 shape vectors as the
-// forward's FP32 layout does, and the FP32 centre coefficient adds them up in member order as
-// the forward's interpolation does); padding gets src -1 and zero coefficients.
-template <typename T>
-__global__ void adj_table_kernel(int64_t N, const int32_t *__restrict__ node_seg, const SegDev *__restrict__ seg,
-                                 const double *__restrict__ w64c, const int32_t *__restrict__ csr_ptr,
-                                 const int32_t *__restrict__ csr_ent, const int64_t *__restrict__ slice,
-                                 int32_t *__restrict__ tsrc, T *__restrict__ tw) {
+__global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, int B, const SegDev *__restrict__ seg,
+                                const uint16_t *__restrict__ rowp, const int64_t *__restrict__ sbeg,
+                                const int32_t *__restrict__ slen, const int32_t *__restrict__ csr_ptr,
+                                const int32_t *__restrict__ csr_ent, const double *__restrict__ w64c,
+                                T *__restrict__ coef) {
     constexpr bool kDev = std::is_same<T, float>::value;
-    // rows N .. 32 ceil(N/32) - 1 of the last slice do not exist: their slots are filled empty
-    const int64_t rows = (N + 31) & ~(int64_t)31;
-    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < rows; m += (int64_t)gridDim.x * blockDim.x) {
-        const bool row = m < N;
-        const SegDev sd = seg[node_seg[row ? m : 0]];
-        const int64_t s = m >> 5, base = slice[s] + (m & 31), len = (slice[s + 1] - slice[s]) >> 5;
+    const int64_t total = (int64_t)ntiles * B;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(g / B), b = (int)(g - (int64_t)t * B);
+        const TileDev tile = tiles[t];
+        const int ws = t * (B / 32) + (b >> 5);
+        const int L = slen[ws];
+        if (L == 0) continue;
+        const bool row = b < tile.count;
+        const SegDev sd = seg[tile.seg];
+        const int64_t m = tile.begin + (row ? rowp[g] : 0);
         const int32_t e0 = row ? csr_ptr[m] : 0, e1 = row ? csr_ptr[m + 1] : 0;
-        for (int64_t t = 0; t < len; ++t) {
-            const int64_t q = base + 32 * t;
-            int32_t src = -1;
+        for (int e = 0; e < L; ++e) {
+            const int64_t q = sbeg[ws] + (b & 31) + (int64_t)32 * e;
             T v[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = T(0);
-            if (e0 + t < e1) {
-                const int64_t e = csr_ent[e0 + t];
-                const int64_t j = e / sd.n, i = e - j * sd.n;
-                src = (int32_t)(sd.off + i);
+            if (e0 + e < e1) {
+                const int64_t ent = csr_ent[e0 + e];
+                const int64_t j = ent / sd.n, i = ent - j * sd.n;
                 const double *wk = w64c + sd.w_off + i;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     if (j > 0 || !kDev) {
                         v[k] = (T)wk[((int64_t)k * sd.K + j) * sd.n];
                     } else {
-                        float ws = 0.f;
-                        for (int jj = 1; jj < sd.K; ++jj) ws += (float)wk[((int64_t)k * sd.K + jj) * sd.n];
-                        v[k] = (T)(1.f - ws);
+                        float wsum = 0.f;
+                        for (int jj = 1; jj < sd.K; ++jj) wsum += (float)wk[((int64_t)k * sd.K + jj) * sd.n];
+                        v[k] = (T)(1.f - wsum);
                     }
                 }
             }
-            tsrc[q] = src;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) tw[q * 8 + k] = v[k];
+            for (int k = 0; k < 8; ++k) coef[q * 8 + k] = v[k];
         }
     }
 }
 
-// grad[2 s + c] += sum over tiles of segment s (in tile order) of partials[2 t + c].
-__global__ void __launch_bounds__(kThreads) grad_finalize_kernel(const TileDev *__restrict__ tiles, int ntiles,
-                                                                  const double *__restrict__ partials,
-                                                                  double *__restrict__ grad) {
-    __shared__ double sh[2 * kThreads];
-    const int s = blockIdx.x;
+// grad[2 s + c] += sum over tiles of segment s of partials[2 t + c], in a fixed order (thread
+// tid adds tiles tid, tid + 1024, ...; then a tree over the threads).  The tile's segment and
+// its partial sums are loaded together, so each pass costs one memory latency.
+constexpr int kFinalizeThreads = 1024;
+__global__ void __launch_bounds__(kFinalizeThreads) grad_finalize_kernel(const TileDev *__restrict__ tiles, int ntiles,
+                                                                          const double *__restrict__ partials,
+                                                                          double *__restrict__ grad) {
+    __shared__ double sh[2][kFinalizeThreads];
+    const int s = blockIdx.x, tid = threadIdx.x;
     double a0 = 0.0, a1 = 0.0;
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
-        if (tiles[t].seg == s) {
-            a0 += partials[2 * t];
-            a1 += partials[2 * t + 1];
+    for (int t = tid; t < ntiles; t += kFinalizeThreads) {
+        const int sg = tiles[t].seg;
+        const double p0 = partials[2 * t], p1 = partials[2 * t + 1];
+        if (sg == s) {
+            a0 += p0;
+            a1 += p1;
         }
-    block_sum2(a0, a1, sh);
-    if (threadIdx.x == 0) {
-        grad[2 * s] += a0;
-        grad[2 * s + 1] += a1;
+    }
+    sh[0][tid] = a0;
+    sh[1][tid] = a1;
+    __syncthreads();
+    for (int h = kFinalizeThreads / 2; h > 0; h >>= 1) {
+        if (tid < h) {
+            sh[0][tid] += sh[0][tid + h];
+            sh[1][tid] += sh[1][tid + h];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        grad[2 * s] += sh[0][0];
+        grad[2 * s + 1] += sh[1][0];
     }
 }
 
@@ -537,42 +578,148 @@ int grid_of(const mlbm_weights *w, const void *fn) {
     return std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
 }
 
+template <typename V_>
+int upload_vec(V_ **dst, const std::vector<V_> &v, const char *what) {
+    if (cudaMalloc(dst, sizeof(V_) * std::max<size_t>(1, v.size())) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return fail(MLBM_ENOMEM, std::string(what) + " allocation failed");
+    }
+    return cuda_check_step(cudaMemcpy(*dst, v.data(), sizeof(V_) * v.size(), cudaMemcpyHostToDevice), what);
+}
+
+// Tables of the transposed interpolation, per forward tile (host arithmetic on the downloaded
+// tile table and transposed stencil): the tile's rows ordered by entry count, longest first
+// (stable), so that the 32 rows of a slice have similar lengths; its reverse halo (own nodes in
+// order, then every other reading node, sorted); per 32-row slice the entry count of its longest
+// row and the slice's first entry; per entry the reading node's reverse-halo slot (0 for
+// padding).  Then the coefficients of the dtype, in a kernel.
 template <typename T>
 int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
-    const int i = std::is_same<T, float>::value ? 0 : 1;
-    if (w->d_adj_tw[i]) return MLBM_OK;
     int rc = MLBM_OK;
-    if (!w->d_adj_slice) {
-        // slice offsets from the row lengths (host arithmetic on the downloaded row pointers)
-        std::vector<int32_t> ptr((size_t)w->N + 1);
-        if ((rc = cuda_check_step(cudaMemcpy(ptr.data(), w->d_csr_ptr, sizeof(int32_t) * ptr.size(),
-                                             cudaMemcpyDeviceToHost), "row pointers")))
+    const int B = w->tile_nodes, WPT = B / 32, nt = w->ntiles;
+    if (!w->d_adj_slot) {
+        std::vector<TileDev> tiles((size_t)nt);
+        std::vector<int32_t> ptr((size_t)w->N + 1), ent((size_t)w->idx_total);
+        if ((rc = cuda_check_step(cudaMemcpy(tiles.data(), w->d_tiles, sizeof(TileDev) * tiles.size(),
+                                             cudaMemcpyDeviceToHost), "tile table")) ||
+            (rc = cuda_check_step(cudaMemcpy(ptr.data(), w->d_csr_ptr, sizeof(int32_t) * ptr.size(),
+                                             cudaMemcpyDeviceToHost), "transposed stencil")) ||
+            (rc = cuda_check_step(cudaMemcpy(ent.data(), w->d_csr_ent, sizeof(int32_t) * ent.size(),
+                                             cudaMemcpyDeviceToHost), "transposed stencil")))
             return rc;
-        const int64_t ns = (w->N + 31) / 32;
-        std::vector<int64_t> off((size_t)ns + 1, 0);
-        for (int64_t s = 0; s < ns; ++s) {
-            int32_t len = 0;
-            for (int64_t m = 32 * s; m < std::min<int64_t>(32 * s + 32, w->N); ++m) len = std::max(len, ptr[m + 1] - ptr[m]);
-            off[s + 1] = off[s] + 32 * (int64_t)len;
+        std::vector<uint16_t> rowp((size_t)nt * B, 0);
+        std::vector<int32_t> slen((size_t)nt * WPT, 0);
+        std::vector<std::vector<int32_t>> rh(nt);
+        std::vector<std::vector<uint16_t>> sl(nt);
+        std::vector<int> bad(nt, 0);
+        auto work = [&](int t0, int t1) {
+            std::vector<int32_t> others;
+            std::vector<int> ord;
+            for (int t = t0; t < t1; ++t) {
+                const TileDev &T_ = tiles[t];
+                const SegmentHost &h = w->seg[T_.seg];
+                auto src_of = [&](int64_t q) { return (int32_t)(h.off + ent[q] % h.n); };
+                const int64_t m0 = T_.begin;
+                ord.resize(T_.count);
+                for (int b = 0; b < T_.count; ++b) ord[b] = b;
+                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+                    return ptr[m0 + x + 1] - ptr[m0 + x] > ptr[m0 + y + 1] - ptr[m0 + y];
+                });
+                others.clear();
+                for (int b = 0; b < T_.count; ++b) {
+                    rowp[(size_t)t * B + b] = (uint16_t)ord[b];
+                    for (int32_t q = ptr[m0 + b]; q < ptr[m0 + b + 1]; ++q) {
+                        const int32_t s = src_of(q);
+                        if (s < m0 || s >= m0 + T_.count) others.push_back(s);
+                    }
+                }
+                std::sort(others.begin(), others.end());
+                others.erase(std::unique(others.begin(), others.end()), others.end());
+                if ((int64_t)T_.count + (int64_t)others.size() > 65535) {
+                    bad[t] = 1;
+                    continue;
+                }
+                std::vector<int32_t> &R = rh[t];
+                R.resize((size_t)T_.count + others.size());
+                for (int b = 0; b < T_.count; ++b) R[b] = (int32_t)(m0 + b);
+                std::copy(others.begin(), others.end(), R.begin() + T_.count);
+                auto slot_of = [&](int32_t s) -> uint16_t {
+                    if (s >= m0 && s < m0 + T_.count) return (uint16_t)(s - m0);
+                    return (uint16_t)(T_.count + (std::lower_bound(others.begin(), others.end(), s) - others.begin()));
+                };
+                int64_t n_ent = 0;
+                for (int ws = 0; ws < WPT; ++ws) {
+                    int L = 0;
+                    for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
+                        const int r = ord[32 * ws + l];
+                        L = std::max(L, (int)(ptr[m0 + r + 1] - ptr[m0 + r]));
+                    }
+                    slen[(size_t)t * WPT + ws] = L;
+                    n_ent += 32 * (int64_t)L;
+                }
+                std::vector<uint16_t> &S = sl[t];
+                S.assign((size_t)n_ent, 0);
+                int64_t base = 0;
+                for (int ws = 0; ws < WPT; ++ws) {
+                    const int L = slen[(size_t)t * WPT + ws];
+                    for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
+                        const int r = ord[32 * ws + l];
+                        for (int32_t q = ptr[m0 + r]; q < ptr[m0 + r + 1]; ++q)
+                            S[base + 32 * (q - ptr[m0 + r]) + l] = slot_of(src_of(q));
+                    }
+                    base += 32 * (int64_t)L;
+                }
+            }
+        };
+        {
+            unsigned hw = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> th;
+            const int chunk = (nt + (int)hw - 1) / (int)hw;
+            for (int t0 = 0; t0 < nt; t0 += chunk) th.emplace_back(work, t0, std::min(nt, t0 + chunk));
+            for (auto &x : th) x.join();
         }
-        w->adj_slots = off[ns];
-        if (cudaMalloc(&w->d_adj_slice, sizeof(int64_t) * off.size()) != cudaSuccess ||
-            cudaMalloc(&w->d_adj_tsrc, sizeof(int32_t) * std::max<int64_t>(1, w->adj_slots)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(MLBM_ENOMEM, "adjoint table allocation failed");
+        for (int t = 0; t < nt; ++t)
+            if (bad[t]) return fail(MLBM_EINVAL, "a tile's reverse halo exceeds 65535 nodes (stencils too spread out)");
+        std::vector<int64_t> roff((size_t)nt), sbeg((size_t)nt * WPT);
+        std::vector<int32_t> rcnt((size_t)nt), rall;
+        std::vector<uint16_t> slots;
+        int rmax = 0;
+        for (int t = 0; t < nt; ++t) {
+            roff[t] = (int64_t)rall.size();
+            rcnt[t] = (int32_t)rh[t].size();
+            rmax = std::max(rmax, rcnt[t]);
+            rall.insert(rall.end(), rh[t].begin(), rh[t].end());
+            int64_t base = (int64_t)slots.size();
+            for (int ws = 0; ws < WPT; ++ws) {
+                sbeg[(size_t)t * WPT + ws] = base;
+                base += 32 * (int64_t)slen[(size_t)t * WPT + ws];
+            }
+            slots.insert(slots.end(), sl[t].begin(), sl[t].end());
+            std::vector<int32_t>().swap(rh[t]);
+            std::vector<uint16_t>().swap(sl[t]);
         }
-        if ((rc = cuda_check_step(cudaMemcpy(w->d_adj_slice, off.data(), sizeof(int64_t) * off.size(),
-                                             cudaMemcpyHostToDevice), "slice offsets")))
+        w->adj_positions = (int64_t)slots.size();
+        w->adj_rmax = rmax;
+        if ((rc = upload_vec(&w->d_adj_rowp, rowp, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_rhalo, rall, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_roff, roff, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_rcnt, rcnt, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_sbeg, sbeg, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_slen, slen, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_slot, slots, "adjoint tables")))
             return rc;
     }
-    if (cudaMalloc(&w->d_adj_tw[i], sizeof(T) * 8 * std::max<int64_t>(1, w->adj_slots)) != cudaSuccess) {
+    const int i = std::is_same<T, float>::value ? 0 : 1;
+    if (w->d_adj_coef[i]) return MLBM_OK;
+    if (cudaMalloc(&w->d_adj_coef[i], sizeof(T) * 8 * (size_t)std::max<int64_t>(1, w->adj_positions)) != cudaSuccess) {
         cudaGetLastError();
-        w->d_adj_tw[i] = nullptr;
+        w->d_adj_coef[i] = nullptr;
         return fail(MLBM_ENOMEM, "adjoint table allocation failed");
     }
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + 31 + 255) / 256, 65536));
-    adj_table_kernel<T><<<grid, 256, 0, st>>>(w->N, w->d_node_seg, w->d_seg, w->d_w64, w->d_csr_ptr, w->d_csr_ent,
-                                              w->d_adj_slice, w->d_adj_tsrc, (T *)w->d_adj_tw[i]);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nt * B + 255) / 256, 65536));
+    adj_coef_kernel<T><<<grid, 256, 0, st>>>(w->d_tiles, nt, B, w->d_seg, w->d_adj_rowp, w->d_adj_sbeg, w->d_adj_slen,
+                                             w->d_csr_ptr, w->d_csr_ent, w->d_w64, (T *)w->d_adj_coef[i]);
     return cuda_check_step(cudaGetLastError(), "adjoint table launch");
 }
 
@@ -591,14 +738,26 @@ int launch_adj_local(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
     return MLBM_OK;
 }
 
-template <typename T, int B>
-int launch_adj_local_next(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
-    const void *fn = (const void *)adj_local_next_kernel<T, B>;
+template <typename T, int B, bool kFromNext>
+int launch_adj_pull(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
+    const size_t smem = (size_t)w->adj_rmax * 8 * sizeof(T);
+    const void *fn = (const void *)adj_pull_kernel<T, B, kFromNext>;
+    int rc = cuda_check_step(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                             "adjoint shared memory");
+    if (rc) return rc;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, 0);
-    const int grid = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
-    adj_local_next_kernel<T, B><<<grid, B, 0, st>>>(a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, smem);
+    if (per_sm < 1) return fail(MLBM_EINVAL, "a tile's reverse halo does not fit in shared memory for the adjoint");
+    const int grid = std::max(1, std::min(w->ntiles, per_sm * w->num_sms));
+    adj_pull_kernel<T, B, kFromNext><<<grid, B, smem, st>>>(a);
     return MLBM_OK;
+}
+
+template <typename T, int B>
+int launch_reverse(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
+    if (a.s_next) return launch_adj_pull<T, B, true>(w, a, st);
+    int rc = launch_adj_local<T, B>(w, a, st);
+    return rc ? rc : launch_adj_pull<T, B, false>(w, a, st);
 }
 
 template <typename T>
@@ -621,21 +780,20 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *s_next, cons
     a.lam_prev = (T *)lam_prev;
     a.mut = (T *)w->d_scratch;
     a.partials = (double *)((char *)w->d_scratch + sizeof(double) * 8 * (size_t)w->N);
-    a.slice = w->d_adj_slice;
-    a.tsrc = w->d_adj_tsrc;
-    a.tw = (const T *)w->d_adj_tw[kDev ? 0 : 1];
+    a.rowp = w->d_adj_rowp;
+    a.rhalo = w->d_adj_rhalo;
+    a.roff = w->d_adj_roff;
+    a.rcnt = w->d_adj_rcnt;
+    a.sbeg = w->d_adj_sbeg;
+    a.slen = w->d_adj_slen;
+    a.slot = w->d_adj_slot;
+    a.coef = (const T *)w->d_adj_coef[kDev ? 0 : 1];
     a.N = w->N;
     a.ntiles = w->ntiles;
-    if (s_next)
-        rc = w->tile_nodes == kTileNodes ? launch_adj_local_next<T, kTileNodes>(w, a, st)
-                                         : launch_adj_local_next<T, kTileNodesSmall>(w, a, st);
-    else
-        rc = w->tile_nodes == kTileNodes ? launch_adj_local<T, kTileNodes>(w, a, st)
-                                         : launch_adj_local<T, kTileNodesSmall>(w, a, st);
+    rc = w->tile_nodes == kTileNodes ? launch_reverse<T, kTileNodes>(w, a, st)
+                                     : launch_reverse<T, kTileNodesSmall>(w, a, st);
     if (rc) return rc;
-    const int tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((w->N + kPullThreads - 1) / kPullThreads, INT32_MAX));
-    adj_transpose_kernel<T><<<tgrid, kPullThreads, 0, st>>>(a);
-    grad_finalize_kernel<<<w->nseg, kThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
+    grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
     return cuda_check_step(cudaGetLastError(), "adjoint launch");
 }
 
@@ -688,7 +846,7 @@ int mlbm_moments_adjoint(const mlbm_weights *w, const mlbm_params *params, int d
         moments_adjoint_kernel<double><<<grid_of(w, (const void *)moments_adjoint_kernel<double>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, w->d_params, (const double *)f, drho, dux, duy,
             (double *)lam, partials, w->N);
-    grad_finalize_kernel<<<w->nseg, kThreads, 0, st>>>(w->d_tiles, w->ntiles, partials, grad);
+    grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, partials, grad);
     return cuda_check_step(cudaGetLastError(), "moments adjoint launch");
 }
 
@@ -713,7 +871,7 @@ int mlbm_init_adjoint(const mlbm_weights *w, const mlbm_params *params, int dtyp
         init_adjoint_kernel<double><<<grid_of(w, (const void *)init_adjoint_kernel<double>), kThreads, 0, st>>>(
             w->d_tiles, w->ntiles, w->d_perm, w->d_fdir64, rho, ux, uy, (const double *)lam0, drho, dux, duy, partials,
             w->N);
-    grad_finalize_kernel<<<w->nseg, kThreads, 0, st>>>(w->d_tiles, w->ntiles, partials, grad);
+    grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, partials, grad);
     return cuda_check_step(cudaGetLastError(), "init adjoint launch");
 }
 

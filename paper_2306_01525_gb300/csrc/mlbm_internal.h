@@ -137,12 +137,21 @@ struct mlbm_weights_impl {
     int64_t nsys = 0;
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
-    // adjoint: transposed-stencil entries sliced by 32 rows (slice offsets, then per entry slot
-    // the reading node and its shape-vector values in FP32 / FP64), tabulated on first use
-    int64_t *d_adj_slice = nullptr;
-    int64_t adj_slots = 0;
-    int32_t *d_adj_tsrc = nullptr;
-    void *d_adj_tw[2] = {nullptr, nullptr};
+    // adjoint, built on first use: per forward tile its rows ordered by transposed-stencil
+    // length ([ntiles][B] offsets), its reverse halo (own nodes, then every other node that reads
+    // one of them, sorted; offset and size per tile), per 32-row slice of that order its first
+    // entry and entries per row ([ntiles][B/32]), per entry the reading node's reverse-halo slot,
+    // and the entries' coefficients in FP32 / FP64 ([entries][8])
+    uint16_t *d_adj_rowp = nullptr;
+    int32_t *d_adj_rhalo = nullptr;
+    int64_t *d_adj_roff = nullptr;
+    int32_t *d_adj_rcnt = nullptr;
+    int64_t *d_adj_sbeg = nullptr;
+    int32_t *d_adj_slen = nullptr;
+    uint16_t *d_adj_slot = nullptr;
+    void *d_adj_coef[2] = {nullptr, nullptr};
+    int64_t adj_positions = 0;
+    int adj_rmax = 0;  // largest reverse halo
     // Shan-Chen steps: [nseg][2] (G, rho_psi) in FP64 then FP32, and the psi scratch [N]
     double *d_sc = nullptr;
     std::vector<double> sc_cache;

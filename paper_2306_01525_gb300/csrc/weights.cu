@@ -408,9 +408,14 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_params);
     cudaFree(w->d_sc);
     cudaFree(w->d_sc_psi);
-    cudaFree(w->d_adj_slice);
-    cudaFree(w->d_adj_tsrc);
-    for (void *b : w->d_adj_tw) cudaFree(b);
+    cudaFree(w->d_adj_rowp);
+    cudaFree(w->d_adj_rhalo);
+    cudaFree(w->d_adj_roff);
+    cudaFree(w->d_adj_rcnt);
+    cudaFree(w->d_adj_sbeg);
+    cudaFree(w->d_adj_slen);
+    cudaFree(w->d_adj_slot);
+    for (void *b : w->d_adj_coef) cudaFree(b);
     for (void *b : w->d_stage) cudaFree(b);
     for (void *q : w->copy_stream)
         if (q) cudaStreamDestroy((cudaStream_t)q);
