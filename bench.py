@@ -696,6 +696,7 @@ def run_mlbm(args):
     gnups64 = N * world * s64 / (ms64 * 1e-3) / 1e9
     # ---------------------------------------------------------------- precision after a run
     err = None
+    err_an = None
     if args.err_steps > 0:
         a32, b32 = fresh(mlbm.F32)
         a64, b64 = fresh(mlbm.F64)
@@ -705,6 +706,14 @@ def run_mlbm(args):
         _, u64, v64 = mlbm.moments(w, params, mlbm.F64, r64)
         s = mlbm.norms(w, u32, u64, v32, v64)
         err = float(np.sqrt(s[0] / s[1]))
+        # the Taylor-Green decay in lattice units, eq. (tgv_eqs): the initial field times
+        # exp(-2 nu (2 pi dx)^2 n), nu = (tau - 1/2) / 3, dx the streaming distance (unit box)
+        decay = float(np.exp(-2.0 * lattice_nu(tau) * (2.0 * np.pi * dx) ** 2 * args.err_steps))
+        ua, va = u_d * decay, v_d * decay
+        err_an = {}
+        for name, (uu, vv) in (("f32", (u32, v32)), ("f64", (u64, v64))):
+            sa = mlbm.norms(w, uu, ua, vv, va)
+            err_an[name] = float(np.sqrt(sa[0] / sa[1]))
         del a32, b32, a64, b64, r32, r64
     # ---------------------------------------------------------------- end to end
     # Through the C ABI with host buffers (mlbm_step_host): every step copies its input state
@@ -786,6 +795,7 @@ def run_mlbm(args):
                  "peak_tflops": 1.25, "frac": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12 / 1.25},
         "speedup_fp32_vs_fp64": gnups32 / gnups64,
         "fp32_vs_fp64_rel_l2_u": err, "error_steps": args.err_steps,
+        "rel_l2_u_vs_analytic": err_an,
         "setup_s": {"cloud_device": t_cloud, "cloud_host": t_cloud_host, "weights_gpu": t_weights},
     }
     line.update(extras)

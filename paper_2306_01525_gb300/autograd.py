@@ -15,7 +15,7 @@ import math
 
 import torch
 
-from . import F32, F64, adjoint_step, init, init_adjoint, moments, moments_adjoint, step
+from . import F32, F64, adjoint_step, init, init_adjoint, moments, moments_adjoint, run, step
 
 
 def _zeros_state(w, dtype, device):
@@ -34,11 +34,11 @@ class _Rollout(torch.autograd.Function):
         init(w, params, dtype, rho0.contiguous(), ux0.contiguous(), uy0.contiguous(), s)
         ckpts = []
         nxt = torch.empty_like(s)
-        for n in range(nsteps):
-            if n % checkpoint == 0:
-                ckpts.append(s.clone())
-            step(w, params, dtype, s, nxt)
-            s, nxt = nxt, s
+        for n0 in range(0, nsteps, checkpoint):
+            ckpts.append(s.clone())
+            # the segment's steps in one library call (graph-captured step loop)
+            if run(w, params, dtype, s, nxt, min(checkpoint, nsteps - n0)) is nxt:
+                s, nxt = nxt, s
         rho, ux, uy = moments(w, params, dtype, s)
         ctx.w, ctx.dtype, ctx.nsteps, ctx.checkpoint = w, dtype, nsteps, checkpoint
         ctx.params = params

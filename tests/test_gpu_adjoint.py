@@ -320,3 +320,39 @@ def test_adjoint_from_next_state_agrees_with_recompute(dtype):
         tol = 1e-11 if dtype == "f64" else 1e-5
         assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < tol
         np.testing.assert_allclose(gb, ga, rtol=tol if dtype == "f64" else 1e-4)
+
+
+@pytest.mark.parametrize("taus", [(0.8, 0.7, 1.3), (0.8, 1.02, 1.3)], ids=["from_next", "recompute"])
+def test_adjoint_step_batched_segments_match_finite_differences(taus):
+    """Three independent runs of uneven size, stencil and degree in one weights object (one
+    reverse step over all their tiles): the transposed step and each segment's dL/dtau and dL/dg
+    against central differences.  With tau = 1.02 in one segment (|1 - 1/tau| < 1/16) the whole
+    call takes the recompute route."""
+    cases = [(16, 12, 2), (20, 16, 3), (12, 9, 2)]
+    parts, segs = [], []
+    for s, (ns, K, deg) in enumerate(cases):
+        parts.append(mi.jittered_lattice(ns, 0.3, seed=90 + s))
+        segs.append(dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=0.7 / ns))
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    w = mlbm.build_weights(mlbm.build_cloud(xy, segs, offs))
+    gs = (2e-5, -1e-5, 3e-5)
+    params = [(t, g, 1.0) for t, g in zip(taus, gs)]
+    s = _rand_state(w, params, xy, seed=31)
+    rng = np.random.default_rng(32)
+    lam = _t(rng.standard_normal(9 * w.n))
+    v = _t(rng.standard_normal(9 * w.n))
+    lam_prev = torch.empty_like(lam)
+    grad = torch.zeros(2 * len(cases), dtype=torch.float64, device=DEV)
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad, s_next=_step(w, params, s))
+    eps = 1e-5
+    fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
+    assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
+    for seg in range(len(cases)):
+        for c, h in ((0, 1e-6), (1, 1e-6)):
+            lo, hi = [list(p) for p in params], [list(p) for p in params]
+            lo[seg][c] -= h
+            hi[seg][c] += h
+            f = (torch.dot(lam, _step(w, [tuple(p) for p in hi], s)) -
+                 torch.dot(lam, _step(w, [tuple(p) for p in lo], s))) / (2 * h)
+            assert float(grad[2 * seg + c]) == pytest.approx(float(f), rel=1e-6), (seg, c)
