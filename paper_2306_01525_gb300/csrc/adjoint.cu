@@ -790,8 +790,7 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *s_next, cons
     a.coef = (const T *)w->d_adj_coef[kDev ? 0 : 1];
     a.N = w->N;
     a.ntiles = w->ntiles;
-    rc = w->tile_nodes == kTileNodes ? launch_reverse<T, kTileNodes>(w, a, st)
-                                     : launch_reverse<T, kTileNodesSmall>(w, a, st);
+    rc = with_tile_nodes(w->tile_nodes, [&](auto Bc) { return launch_reverse<T, decltype(Bc)::value>(w, a, st); });
     if (rc) return rc;
     grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
     return cuda_check_step(cudaGetLastError(), "adjoint launch");

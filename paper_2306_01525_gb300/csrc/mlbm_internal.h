@@ -1,10 +1,12 @@
 // Internal structures of the GB300 meshless LBM library (not part of the C ABI).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <map>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/mlbm.h"
@@ -58,9 +60,39 @@ struct SegDev {
 };
 
 // Nodes per tile of the fused step (one CTA pass over a contiguous Morton run): large tiles
-// for clouds with enough tiles to fill the GPU, small tiles otherwise.
+// for clouds with enough tiles to fill the GPU, small tiles otherwise, and one-warp tiles for
+// clouds so small that 128-node tiles would leave SMs idle or doubly loaded (a 20 k-node cloud
+// makes 156 such tiles for 152 SMs).
 constexpr int kTileNodes = 512;
 constexpr int kTileNodesSmall = 128;
+constexpr int kTileNodesTiny = 32;
+
+// CTAs per SM that the tile kernels' register budget is set for: two 512-node CTAs per SM in
+// FP32 (one in FP64), the same threads per SM for 128-node tiles, at most 16 one-warp CTAs.
+constexpr int tile_min_blocks(int B, int elem_bytes) {
+    return std::min((elem_bytes == 4 ? 2 : 1) * (kTileNodes / B), 16);
+}
+
+// Tile size for a cloud whose segments have the given node counts.
+inline int choose_tile_nodes(const std::vector<int64_t> &seg_nodes, int num_sms) {
+    int64_t big = 0, small = 0;
+    for (int64_t n : seg_nodes) {
+        big += (n + kTileNodes - 1) / kTileNodes;
+        small += (n + kTileNodesSmall - 1) / kTileNodesSmall;
+    }
+    const int64_t sms = std::max(1, num_sms);
+    if (big >= 4 * sms) return kTileNodes;
+    if (small >= 2 * sms) return kTileNodesSmall;
+    return kTileNodesTiny;
+}
+
+// f(std::integral_constant<int, B>{}) for the tile size B of the weights (kernel dispatch).
+template <typename F>
+int with_tile_nodes(int tile_nodes, F &&f) {
+    if (tile_nodes == kTileNodes) return f(std::integral_constant<int, kTileNodes>{});
+    if (tile_nodes == kTileNodesSmall) return f(std::integral_constant<int, kTileNodesSmall>{});
+    return f(std::integral_constant<int, kTileNodesTiny>{});
+}
 
 // A tile: a contiguous run of stored nodes of one segment processed by one CTA pass.
 // Its halo (the tile's own nodes first, then every other node its stencils read, sorted) is

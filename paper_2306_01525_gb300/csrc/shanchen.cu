@@ -65,7 +65,7 @@ __device__ __forceinline__ T sc_exp(T x) {
 
 // Pass 1: fhat of every node of the tile (storage form) into fout, psi(rho of fhat) into psi.
 template <typename T, int B>
-__global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)) sc_stream_kernel(ScArgs<T> a) {
+__global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_stream_kernel(ScArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)
 // Pass 2: psi at the eight departure points of every node, the interaction force, and the
 // collision of fhat (read from and written back to fout) towards the shifted equilibrium.
 template <typename T, int B>
-__global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)) sc_collide_kernel(ScArgs<T> a) {
+__global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_collide_kernel(ScArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
@@ -291,7 +291,7 @@ int sc_step_t(mlbm_weights *w, const void *fin, void *fout, void *mom, cudaStrea
     a.mom = (T *)mom;
     a.N = w->N;
     a.ntiles = w->ntiles;
-    return w->tile_nodes == kTileNodes ? launch_sc_t<T, kTileNodes>(w, a, st) : launch_sc_t<T, kTileNodesSmall>(w, a, st);
+    return with_tile_nodes(w->tile_nodes, [&](auto Bc) { return launch_sc_t<T, decltype(Bc)::value>(w, a, st); });
 }
 
 }  // namespace

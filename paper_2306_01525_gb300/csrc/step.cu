@@ -110,7 +110,7 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
 //      FP64: fhat_k(i) = sum_{j>=0} W_k[j](i) f_k(s_j(i)) as written in eq. (shape_vector);
 //   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
 template <typename T, int B>
-__global__ void __launch_bounds__(B, (sizeof(T) == 4 ? 2 : 1) * (kTileNodes / B)) step_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) step_kernel(StepArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
@@ -378,19 +378,24 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.N = w->N;
     a.ntiles = w->ntiles;
     const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
-    if (w->tile_nodes == kTileNodes)
-        step_kernel<T, kTileNodes><<<grid, kTileNodes, step_smem<T>(w), st>>>(a);
-    else
-        step_kernel<T, kTileNodesSmall><<<grid, kTileNodesSmall, step_smem<T>(w), st>>>(a);
-    return cuda_check_step(cudaGetLastError(), "step_kernel launch");
+    const size_t smem = step_smem<T>(w);
+    return with_tile_nodes(w->tile_nodes, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        step_kernel<T, B><<<grid, B, smem, st>>>(a);
+        return cuda_check_step(cudaGetLastError(), "step_kernel launch");
+    });
 }
 
 // Persistent grids of the step kernels: CTAs resident per SM x SMs, capped by the tile count.
 // A precision whose halo does not fit in shared memory gets grid 0 and is refused by the step.
 int prepare_step_grids(mlbm_weights *w) {
-    const bool big = w->tile_nodes == kTileNodes;
-    const void *fns[2] = {big ? (const void *)step_kernel<float, kTileNodes> : (const void *)step_kernel<float, kTileNodesSmall>,
-                          big ? (const void *)step_kernel<double, kTileNodes> : (const void *)step_kernel<double, kTileNodesSmall>};
+    const void *fns[2] = {nullptr, nullptr};
+    with_tile_nodes(w->tile_nodes, [&](auto Bc) {
+        constexpr int B = decltype(Bc)::value;
+        fns[0] = (const void *)step_kernel<float, B>;
+        fns[1] = (const void *)step_kernel<double, B>;
+        return 0;
+    });
     const size_t sm[2] = {step_smem<float>(w), step_smem<double>(w)};
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);

@@ -679,11 +679,10 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
     w->perm = c->perm;
     w->idx_total = c->idx_total;
     w->w_total = c->w_total;
-    // large tiles when the cloud has at least four per SM, small ones otherwise
     {
-        int64_t big = 0;
-        for (auto &h : c->seg) big += (h.n + kTileNodes - 1) / kTileNodes;
-        w->tile_nodes = big >= 4LL * std::max(1, w->num_sms) ? kTileNodes : kTileNodesSmall;
+        std::vector<int64_t> ns;
+        for (auto &h : c->seg) ns.push_back(h.n);
+        w->tile_nodes = choose_tile_nodes(ns, w->num_sms);
     }
     int rc = upload_monomial_tables();
     // segment table
