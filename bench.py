@@ -472,6 +472,49 @@ def bench_shan_chen(n_side: int = 2048, steps: int = 200, warmup: int = 5):
             "dtype": "f32", "G": sc[0]}
 
 
+def bench_tgv_small(steps: int = 500, reps: int = 20):
+    """The paper's Taylor-Green case as configured for plain MLBM in FP64: 32 x 32 jittered
+    lattice (1024 nodes), N_L 12, P_2, tau 0.8, u0 0.01, dx_ml = h, 500 steps; a cloud this small
+    is latency-bound, so the figure is the time of the whole 500-step run (graph-captured step
+    loop), its GNUPS, and the L2 error of u against the analytic decay at the end."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    wl = WORKLOADS["tgv_small"]
+    n_side, K, deg, tau, u0 = wl["n_side"], wl["K"], wl["deg"], wl["tau"], wl["u0"]
+    dx = 1.0 / n_side
+    xy = mi.jittered_lattice(n_side, 0.3, seed=wl["seed"])
+    w = mlbm.build_weights(mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K,
+                                                     degree=deg, dx_ml=dx)))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = (torch.as_tensor(a, dtype=torch.float64, device=dev) for a in mi.tgv_initial(xy, u0))
+    a = torch.empty(9 * w.n, dtype=torch.float64, device=dev)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F64, rho, u, v, a)
+    mlbm.run(w, params, mlbm.F64, a, b, 64)  # graph capture and warm-up
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(reps):
+        mlbm.init(w, params, mlbm.F64, rho, u, v, a)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = mlbm.run(w, params, mlbm.F64, a, b, steps)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.median(times))
+    _, uu, vv = mlbm.moments(w, params, mlbm.F64, res)
+    decay = float(np.exp(-2.0 * lattice_nu(tau) * (2.0 * np.pi * dx) ** 2 * steps))
+    sn = mlbm.norms(w, uu, u * decay, vv, v * decay)
+    return {"workload": "tgv_32sq_k12_d2", "nodes": w.n, "steps": steps, "dtype": "f64",
+            "run_ms": ms, "us_per_step": ms * 1e3 / steps, "value": w.n * steps / (ms * 1e-3) / 1e9,
+            "unit": UNIT, "rel_l2_u_vs_analytic": float(np.sqrt(sn[0] / sn[1])),
+            "timing": "median of %d runs, CUDA events" % reps}
+
+
 def bench_lattice(n_side: int = 2048, steps: int = 200, warmup: int = 5):
     """Standard lattice LBM (index-shift streaming) on an n_side^2 periodic lattice, FP32: the
     paper's comparison method at the node count of the headline workload."""
@@ -770,6 +813,8 @@ def run_mlbm(args):
         torch.cuda.empty_cache()
         extras["lattice_lbm"] = bench_lattice()
         torch.cuda.empty_cache()
+        extras["tgv_small"] = bench_tgv_small()
+        torch.cuda.empty_cache()
         extras["shan_chen"] = bench_shan_chen()
         torch.cuda.empty_cache()
         extras["paper_sweep"] = bench_paper_sweep("f64")
@@ -820,7 +865,7 @@ def main():
                     help="stencil rule of the main workload (own-node or nearest-node)")
     ap.add_argument("--ratio", type=float, default=1.0, help="dx_ml / h of the main workload")
     ap.add_argument("--leg", default=None,
-                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep"],
+                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep", "tgv_small"],
                     help="run only this extra measurement and print it")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep, annulus and adjoint measurements")
@@ -833,7 +878,7 @@ def main():
         import torch
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        legs = {"batched": lambda: bench_batched(1000), "annulus": bench_annulus,
+        legs = {"batched": lambda: bench_batched(1000), "annulus": bench_annulus, "tgv_small": bench_tgv_small,
                 "adjoint": lambda: bench_adjoint(2000), "lattice_lbm": bench_lattice,
                 "shan_chen": bench_shan_chen,
                 "paper_sweep": lambda: bench_paper_sweep("f64")}
