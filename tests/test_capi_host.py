@@ -175,3 +175,11 @@ def test_departure_nodes_match_oracle_nearest_rule(geometry):
     np.testing.assert_array_equal(c.departure_nodes(0), sidx[1:, 0, :])
     own = mlbm.build_cloud(xy, dict(seg, stencil_mode=mlbm.STENCIL_OWN))
     assert np.all(own.departure_nodes(0) == np.arange(xy.shape[1])[None, :])
+
+
+def test_empty_cloud_rejected():
+    """A cloud without nodes has no stencils: the build refuses it instead of returning an
+    empty object."""
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.build_cloud(np.zeros((2, 0)), _periodic(9, 2, 0.1))
+    assert e.value.code == mlbm.EINVAL

@@ -295,6 +295,18 @@ def test_run_graph_equals_repeated_steps():
         assert torch.equal(res, ga)
 
 
+def test_run_of_zero_steps_returns_the_input_untouched():
+    xy, dx, cloud, w = _setup_tgv(16, 12, 2)
+    params = [(0.8, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01)
+    for dtype in (mlbm.F32, mlbm.F64):
+        fa = _gpu_init(w, params, dtype, rho, u, v)
+        keep = fa.clone()
+        fb = torch.full_like(fa, 7.0)
+        res = mlbm.run(w, params, dtype, fa, fb, 0)
+        assert res is fa and torch.equal(fa, keep) and bool((fb == 7.0).all())
+
+
 def test_ragged_tail_and_minimal_segment():
     """N not a multiple of the 256-node tile and a segment with exactly N_L nodes."""
     parts = [mi.jittered_lattice(31, 0.3, seed=5), mi.jittered_lattice(3, 0.2, seed=6)]
