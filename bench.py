@@ -324,7 +324,8 @@ def bench_annulus(max_steps: int = 500000, chunk: int = 2000):
     want = np.abs(annulus_profile(r / dx, g, lattice_nu(tau), 0.5 / dx, 1.0 / dx))
     uu, vv = u.cpu().numpy(), v.cpu().numpy()
     err = float(np.sqrt(np.sum((np.hypot(uu, vv) - want) ** 2) / np.sum(want ** 2)))
-    return {"workload": "annulus_20k_k20_d3", "nodes": n, "steps": done, "residual_per_step": res,
+    return {"workload": "annulus_20k_k20_d3", "nodes": n, "steps": done,
+            "residual_per_step": res if np.isfinite(res) else None,
             "l2_speed_vs_analytic": err, "value": n * done / el / 1e9, "unit": UNIT,
             "ms_per_step": el / done * 1e3, "dtype": "f64",
             "note": "wall time of the whole run incl. residual checks every %d steps" % chunk}
@@ -878,6 +879,8 @@ def main():
     ap.add_argument("--leg", default=None,
                     choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep", "tgv_small"],
                     help="run only this extra measurement and print it")
+    ap.add_argument("--leg-steps", type=int, default=None,
+                    help="with --leg: the leg's step count (annulus: its step cap), e.g. for a short ncu capture")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-sweep, annulus and adjoint measurements")
     args = ap.parse_args()
@@ -889,8 +892,11 @@ def main():
         import torch
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        legs = {"batched": lambda: bench_batched(1000), "annulus": bench_annulus, "tgv_small": bench_tgv_small,
-                "adjoint": lambda: bench_adjoint(2000), "lattice_lbm": bench_lattice,
+        n = args.leg_steps
+        legs = {"batched": lambda: bench_batched(n or 1000),
+                "annulus": lambda: bench_annulus(n or 500000, min(2000, n or 2000)),
+                "tgv_small": lambda: bench_tgv_small(n or 500),
+                "adjoint": lambda: bench_adjoint(n or 2000), "lattice_lbm": bench_lattice,
                 "shan_chen": bench_shan_chen,
                 "paper_sweep": lambda: bench_paper_sweep("f64")}
         print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
