@@ -43,6 +43,7 @@ struct StepArgs {
     T *__restrict__ mom;  // optional [3][N]
     int64_t N;
     int ntiles;
+    int umax;  // largest halo (slots): split tiles keep their hand-over buffer after it
 };
 
 // Nearest-node stencils (Sec. 2.3, appendix algorithm): population k of node b is interpolated
@@ -101,8 +102,52 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
     for (int k = 0; k < 8; ++k) f[k + 1] = kLiteral ? acc[k] : c[k] + acc[k];
 }
 
+// Own-stencil interpolation of the direction vectors Q0 .. Q0 + NQ - 1 of node b over members
+// 1..m1, in interp_own's order (members in sequence, two per slot word), so a node whose
+// directions are split over two threads gets the same sums as one thread computing all.
+template <typename T, int B, int Q0, int NQ>
+__device__ __forceinline__ void interp_own_part(const typename V<T>::type *__restrict__ wp,
+                                                const uint32_t *__restrict__ lp, const typename V<T>::type *sh,
+                                                const typename V<T>::type (&c)[8 / V<T>::width],
+                                                typename V<T>::type (&acc)[8 / V<T>::width], int m1) {
+    using VT = typename V<T>::type;
+    constexpr bool kLiteral = !std::is_same<T, float>::value;
+    constexpr int NV = 8 / V<T>::width;
+    int j = 0;
+#pragma unroll 2
+    for (; j + 1 < m1; j += 2) {
+        const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
+        VT w0[NQ], w1[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            w0[q] = __ldcs(wp + (int64_t)(j * NV + Q0 + q) * B);
+            w1[q] = __ldcs(wp + (int64_t)((j + 1) * NV + Q0 + q) * B);
+        }
+        const int s0 = (int)(pr & 0xFFFFu), s1 = (int)(pr >> 16);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) vfma<kLiteral>(acc[Q0 + q], w0[q], sh[s0 * NV + Q0 + q], c[Q0 + q]);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) vfma<kLiteral>(acc[Q0 + q], w1[q], sh[s1 * NV + Q0 + q], c[Q0 + q]);
+    }
+    if (j < m1) {
+        const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
+        const int s0 = (int)(pr & 0xFFFFu);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            vfma<kLiteral>(acc[Q0 + q], __ldcs(wp + (int64_t)(j * NV + Q0 + q) * B), sh[s0 * NV + Q0 + q], c[Q0 + q]);
+    }
+}
+
+// Threads per CTA of the step kernel: one per node, except one-warp tiles, whose nodes get two
+// threads each (the halves of the eight directions), so that small clouds, a few warps per SM,
+// hide the latency of their dependent operations with twice the warps.
+__host__ __device__ constexpr int step_threads(int B) { return B == kTileNodesTiny ? 2 * B : B; }
+__host__ __device__ constexpr int step_min_blocks(int B, int elem_bytes) {
+    return B == kTileNodesTiny ? 8 : tile_min_blocks(B, elem_bytes);
+}
+
 // One fused time step over all tiles (persistent CTAs, one node per thread, B threads per CTA
-// and B nodes per tile):
+// and B nodes per tile; for one-warp tiles two threads per node, see step_threads):
 //   1. stage f^post_k (k = 1..8) of the tile's halo in shared memory as [slot][8];
 //   2. FP32: fhat_k(i) = f_k(i) + sum_{j>=1} W_k[j](i) (f_k(s_j(i)) - f_k(i)) -- the shape vector
 //      sums to one (constant reproduction), so the centre weight is implied and never loaded,
@@ -110,14 +155,18 @@ __device__ __forceinline__ void interp_nearest(const StepArgs<T> &a, const TileD
 //      FP64: fhat_k(i) = sum_{j>=0} W_k[j](i) f_k(s_j(i)) as written in eq. (shape_vector);
 //   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
 template <typename T, int B>
-__global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) step_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(step_threads(B), step_min_blocks(B, (int)sizeof(T))) step_kernel(StepArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;  // vectors per 8 moving populations
+    constexpr bool kSplit = step_threads(B) != B;
+    constexpr int NQ = kSplit ? NV / 2 : NV;  // vectors per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     const int64_t N = a.N;
+    // split tiles: the second half's interpolated populations, handed to the first, [B][NQ]
+    VT *hand = sh + (size_t)a.umax * NV;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
         // 1. halo staging (own nodes first, then the other members sorted: mostly coalesced)
@@ -126,16 +175,14 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) step_ke
         else
             stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
         __syncthreads();
-        const int b = threadIdx.x;
-        if (b < tile.count) {
-            const int64_t p = tile.begin + b;
+        if constexpr (kSplit) {
+            const int b = kSplit ? (int)threadIdx.x % B : (int)threadIdx.x;
+            const int half = kSplit ? (int)threadIdx.x / B : 0;  // split tiles: vectors half * NQ ..
+            const bool own = tile.mode != MLBM_STENCIL_NEAREST;
             T f[9];
-            f[0] = a.fin[p];
-            if (tile.mode == MLBM_STENCIL_NEAREST) {
-                interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
-            } else {
+            if (b < tile.count && own) {
                 VT c[NV], acc[NV];
-#pragma unroll
+    #pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     c[q] = sh[b * NV + q];
                     vzero(acc[q]);
@@ -145,56 +192,159 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) step_ke
                 if constexpr (kLiteral) {
                     // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
                     wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
+    #pragma unroll
+                    for (int q = 0; q < NV; ++q)
+                        if (!kSplit || q / NQ == half) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
                     wp += (int64_t)NV * B;
                 } else {
                     wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
                 }
                 // 2. interpolation over stencil members 1..K-1, two members per packed slot word
-                VT unused[NV];
-                interp_own<T, B, false>(wp, lp, sh, c, acc, unused, tile.K - 1);
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    if constexpr (kLiteral)
-                        vunpack(f + 1 + q * W, acc[q]);
+                if constexpr (kSplit) {
+                    if (half == 0)
+                        interp_own_part<T, B, 0, NQ>(wp, lp, sh, c, acc, tile.K - 1);
                     else
-                        vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+                        interp_own_part<T, B, NQ, NQ>(wp, lp, sh, c, acc, tile.K - 1);
+                } else {
+                    VT unused[NV];
+                    interp_own<T, B, false>(wp, lp, sh, c, acc, unused, tile.K - 1);
                 }
-            }  // own-stencil interpolation
-            // 3. wall bounce-back: unknown populations take the streamed opposite population
-            if (a.mask) {
-                const uint16_t mb = a.mask[p];
-                if (mb) {
-                    T g[9];
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) g[k] = f[k];
-#pragma unroll
-                    for (int k = 1; k < 9; ++k)
-                        if (mb >> k & 1u) f[k] = g[opp_of(k)];
+                if (kSplit && half == 1) {
+                    if constexpr (kSplit) {
+    #pragma unroll
+                        for (int q = 0; q < NQ; ++q) {
+                            VT v = acc[NQ + q];
+                            if constexpr (!kLiteral)
+                                v = make_float4(c[NQ + q].x + v.x, c[NQ + q].y + v.y, c[NQ + q].z + v.z, c[NQ + q].w + v.w);
+                            hand[b * NQ + q] = v;
+                        }
+                    }
+                } else {
+    #pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        if constexpr (kLiteral)
+                            vunpack(f + 1 + q * W, acc[q]);
+                        else
+                            vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+                    }
                 }
             }
-            // 4. collision
-            const T *pr = a.params + 4 * tile.seg;
-            const T inv_tau = pr[3];
-            const T gm = pr[1];
-            T gx = T(0), gy = T(0);
-            if (gm != T(0)) {
-                gx = gm * a.fdir[p];
-                gy = gm * a.fdir[N + p];
+            if constexpr (kSplit) __syncthreads();  // the second half's populations are in hand[]
+            if (b < tile.count && half == 0) {
+                const int64_t p = tile.begin + b;
+                f[0] = a.fin[p];
+                if (!own) {
+                    interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
+                } else if constexpr (kSplit) {
+    #pragma unroll
+                    for (int q = 0; q < NQ; ++q) vunpack(f + 1 + (NQ + q) * W, hand[b * NQ + q]);
+                }
+                // 3. wall bounce-back: unknown populations take the streamed opposite population
+                if (a.mask) {
+                    const uint16_t mb = a.mask[p];
+                    if (mb) {
+                        T g[9];
+    #pragma unroll
+                        for (int k = 0; k < 9; ++k) g[k] = f[k];
+    #pragma unroll
+                        for (int k = 1; k < 9; ++k)
+                            if (mb >> k & 1u) f[k] = g[opp_of(k)];
+                    }
+                }
+                // 4. collision
+                const T *pr = a.params + 4 * tile.seg;
+                const T inv_tau = pr[3];
+                const T gm = pr[1];
+                T gx = T(0), gy = T(0);
+                if (gm != T(0)) {
+                    gx = gm * a.fdir[p];
+                    gy = gm * a.fdir[N + p];
+                }
+                T rho, ux, uy;
+                if constexpr (std::is_same<T, float>::value)
+                    collide_projected(f, pr[2], inv_tau, gx, gy, rho, ux, uy);
+                else
+                    collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
+                // 5. store
+    #pragma unroll
+                for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
+                if (a.mom) {
+                    a.mom[p] = rho;
+                    a.mom[N + p] = ux;
+                    a.mom[2 * N + p] = uy;
+                }
             }
-            T rho, ux, uy;
-            if constexpr (std::is_same<T, float>::value)
-                collide_projected(f, pr[2], inv_tau, gx, gy, rho, ux, uy);
-            else
-                collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
-            // 5. store
-#pragma unroll
-            for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
-            if (a.mom) {
-                a.mom[p] = rho;
-                a.mom[N + p] = ux;
-                a.mom[2 * N + p] = uy;
+        } else {
+            const int b = threadIdx.x;
+            if (b < tile.count) {
+                const int64_t p = tile.begin + b;
+                T f[9];
+                f[0] = a.fin[p];
+                if (tile.mode == MLBM_STENCIL_NEAREST) {
+                    interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
+                } else {
+                    VT c[NV], acc[NV];
+    #pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        c[q] = sh[b * NV + q];
+                        vzero(acc[q]);
+                    }
+                    const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+                    const VT *__restrict__ wp;
+                    if constexpr (kLiteral) {
+                        // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
+                        wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
+    #pragma unroll
+                        for (int q = 0; q < NV; ++q) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
+                        wp += (int64_t)NV * B;
+                    } else {
+                        wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+                    }
+                    // 2. interpolation over stencil members 1..K-1, two members per packed slot word
+                    VT unused[NV];
+                    interp_own<T, B, false>(wp, lp, sh, c, acc, unused, tile.K - 1);
+    #pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        if constexpr (kLiteral)
+                            vunpack(f + 1 + q * W, acc[q]);
+                        else
+                            vunpack_sum(f + 1 + q * W, c[q], acc[q]);
+                    }
+                }  // own-stencil interpolation
+                // 3. wall bounce-back: unknown populations take the streamed opposite population
+                if (a.mask) {
+                    const uint16_t mb = a.mask[p];
+                    if (mb) {
+                        T g[9];
+    #pragma unroll
+                        for (int k = 0; k < 9; ++k) g[k] = f[k];
+    #pragma unroll
+                        for (int k = 1; k < 9; ++k)
+                            if (mb >> k & 1u) f[k] = g[opp_of(k)];
+                    }
+                }
+                // 4. collision
+                const T *pr = a.params + 4 * tile.seg;
+                const T inv_tau = pr[3];
+                const T gm = pr[1];
+                T gx = T(0), gy = T(0);
+                if (gm != T(0)) {
+                    gx = gm * a.fdir[p];
+                    gy = gm * a.fdir[N + p];
+                }
+                T rho, ux, uy;
+                if constexpr (std::is_same<T, float>::value)
+                    collide_projected(f, pr[2], inv_tau, gx, gy, rho, ux, uy);
+                else
+                    collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
+                // 5. store
+    #pragma unroll
+                for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
+                if (a.mom) {
+                    a.mom[p] = rho;
+                    a.mom[N + p] = ux;
+                    a.mom[2 * N + p] = uy;
+                }
             }
         }
         __syncthreads();
@@ -359,7 +509,8 @@ int check_dtype(const mlbm_weights *w, int dtype) {
 
 template <typename T>
 size_t step_smem(const mlbm_weights *w) {
-    return (size_t)w->umax * 8 * sizeof(T);
+    const size_t hand = w->tile_nodes == kTileNodesTiny ? (size_t)kTileNodesTiny * 4 * sizeof(T) : 0;
+    return (size_t)w->umax * 8 * sizeof(T) + hand;
 }
 
 template <typename T>
@@ -377,11 +528,12 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.mom = (T *)mom;
     a.N = w->N;
     a.ntiles = w->ntiles;
+    a.umax = w->umax;
     const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
     const size_t smem = step_smem<T>(w);
     return with_tile_nodes(w->tile_nodes, [&](auto Bc) {
         constexpr int B = decltype(Bc)::value;
-        step_kernel<T, B><<<grid, B, smem, st>>>(a);
+        step_kernel<T, B><<<grid, step_threads(B), smem, st>>>(a);
         return cuda_check_step(cudaGetLastError(), "step_kernel launch");
     });
 }
@@ -406,7 +558,7 @@ int prepare_step_grids(mlbm_weights *w) {
                                  "step shared-memory attribute");
         if (rc) return rc;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], w->tile_nodes, sm[i]);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], step_threads(w->tile_nodes), sm[i]);
         w->step_grid[i] = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
     }
     return MLBM_OK;
