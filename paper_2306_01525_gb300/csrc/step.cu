@@ -138,12 +138,15 @@ __device__ __forceinline__ void interp_own_part(const typename V<T>::type *__res
     }
 }
 
-// Threads per CTA of the step kernel: one per node, except one-warp tiles, whose nodes get two
-// threads each (the halves of the eight directions), so that small clouds, a few warps per SM,
-// hide the latency of their dependent operations with twice the warps.
-__host__ __device__ constexpr int step_threads(int B) { return B == kTileNodesTiny ? 2 * B : B; }
+// Threads per node of the step kernel: one, except in one-warp tiles, whose nodes get one thread
+// per 16-byte vector of their eight directions (two in FP32, four in FP64), so that small
+// clouds, a few warps per SM, hide the latency of their dependent operations with more warps.
+__host__ __device__ constexpr int step_split(int B, int elem_bytes) {
+    return B == kTileNodesTiny ? (elem_bytes == 8 ? 4 : 2) : 1;
+}
+__host__ __device__ constexpr int step_threads(int B, int elem_bytes) { return B * step_split(B, elem_bytes); }
 __host__ __device__ constexpr int step_min_blocks(int B, int elem_bytes) {
-    return B == kTileNodesTiny ? 8 : tile_min_blocks(B, elem_bytes);
+    return B == kTileNodesTiny ? 16 / step_split(B, elem_bytes) : tile_min_blocks(B, elem_bytes);
 }
 
 // One fused time step over all tiles (persistent CTAs, one node per thread, B threads per CTA
@@ -155,17 +158,19 @@ __host__ __device__ constexpr int step_min_blocks(int B, int elem_bytes) {
 //      FP64: fhat_k(i) = sum_{j>=0} W_k[j](i) f_k(s_j(i)) as written in eq. (shape_vector);
 //   3. bounce-back of unknown wall populations; 4. BGK collision with forcing; 5. store.
 template <typename T, int B>
-__global__ void __launch_bounds__(step_threads(B), step_min_blocks(B, (int)sizeof(T))) step_kernel(StepArgs<T> a) {
+__global__ void __launch_bounds__(step_threads(B, (int)sizeof(T)), step_min_blocks(B, (int)sizeof(T)))
+    step_kernel(StepArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
     constexpr int W = V<T>::width;
     constexpr int NV = 8 / W;  // vectors per 8 moving populations
-    constexpr bool kSplit = step_threads(B) != B;
-    constexpr int NQ = kSplit ? NV / 2 : NV;  // vectors per thread
+    constexpr int S = step_split(B, (int)sizeof(T));  // threads per node
+    constexpr bool kSplit = S > 1;
+    constexpr int NQ = NV / S;  // direction vectors per thread
     extern __shared__ __align__(16) unsigned char smem_raw[];
     VT *sh = reinterpret_cast<VT *>(smem_raw);  // [U][NV]
     const int64_t N = a.N;
-    // split tiles: the second half's interpolated populations, handed to the first, [B][NQ]
+    // split tiles: the other threads' interpolated populations, handed to the first, [B][NV]
     VT *hand = sh + (size_t)a.umax * NV;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
@@ -176,13 +181,16 @@ __global__ void __launch_bounds__(step_threads(B), step_min_blocks(B, (int)sizeo
             stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
         __syncthreads();
         if constexpr (kSplit) {
-            const int b = kSplit ? (int)threadIdx.x % B : (int)threadIdx.x;
-            const int half = kSplit ? (int)threadIdx.x / B : 0;  // split tiles: vectors half * NQ ..
+            // S threads per node: thread part r interpolates the direction vectors r NQ ..
+            // (r + 1) NQ - 1 over all members, in the one-thread order; part 0 collects the
+            // others' populations from hand[] and collides
+            const int b = (int)threadIdx.x % B;
+            const int part = (int)threadIdx.x / B;
             const bool own = tile.mode != MLBM_STENCIL_NEAREST;
             T f[9];
             if (b < tile.count && own) {
                 VT c[NV], acc[NV];
-    #pragma unroll
+#pragma unroll
                 for (int q = 0; q < NV; ++q) {
                     c[q] = sh[b * NV + q];
                     vzero(acc[q]);
@@ -192,61 +200,50 @@ __global__ void __launch_bounds__(step_threads(B), step_min_blocks(B, (int)sizeo
                 if constexpr (kLiteral) {
                     // FP64: literal sum over members 0..K-1; row 0 holds the centre weight
                     wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
-    #pragma unroll
+#pragma unroll
                     for (int q = 0; q < NV; ++q)
-                        if (!kSplit || q / NQ == half) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
+                        if (q / NQ == part) vmul(acc[q], __ldcs(wp + (int64_t)q * B), c[q]);
                     wp += (int64_t)NV * B;
                 } else {
                     wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
                 }
                 // 2. interpolation over stencil members 1..K-1, two members per packed slot word
-                if constexpr (kSplit) {
-                    if (half == 0)
-                        interp_own_part<T, B, 0, NQ>(wp, lp, sh, c, acc, tile.K - 1);
-                    else
-                        interp_own_part<T, B, NQ, NQ>(wp, lp, sh, c, acc, tile.K - 1);
-                } else {
-                    VT unused[NV];
-                    interp_own<T, B, false>(wp, lp, sh, c, acc, unused, tile.K - 1);
+                switch (part) {
+                    case 0: interp_own_part<T, B, 0, NQ>(wp, lp, sh, c, acc, tile.K - 1); break;
+                    case 1: interp_own_part<T, B, 1 * NQ, NQ>(wp, lp, sh, c, acc, tile.K - 1); break;
+                    case 2: interp_own_part<T, B, (2 * NQ) % NV, NQ>(wp, lp, sh, c, acc, tile.K - 1); break;
+                    default: interp_own_part<T, B, (3 * NQ) % NV, NQ>(wp, lp, sh, c, acc, tile.K - 1); break;
                 }
-                if (kSplit && half == 1) {
-                    if constexpr (kSplit) {
-    #pragma unroll
-                        for (int q = 0; q < NQ; ++q) {
-                            VT v = acc[NQ + q];
-                            if constexpr (!kLiteral)
-                                v = make_float4(c[NQ + q].x + v.x, c[NQ + q].y + v.y, c[NQ + q].z + v.z, c[NQ + q].w + v.w);
-                            hand[b * NQ + q] = v;
-                        }
-                    }
-                } else {
-    #pragma unroll
-                    for (int q = 0; q < NQ; ++q) {
-                        if constexpr (kLiteral)
-                            vunpack(f + 1 + q * W, acc[q]);
-                        else
-                            vunpack_sum(f + 1 + q * W, c[q], acc[q]);
-                    }
+#pragma unroll
+                for (int q = 0; q < NV; ++q) {
+                    if (q / NQ != part) continue;
+                    VT v = acc[q];
+                    if constexpr (!kLiteral)
+                        v = make_float4(c[q].x + v.x, c[q].y + v.y, c[q].z + v.z, c[q].w + v.w);
+                    if (part == 0)
+                        vunpack(f + 1 + q * W, v);
+                    else
+                        hand[b * NV + q] = v;
                 }
             }
-            if constexpr (kSplit) __syncthreads();  // the second half's populations are in hand[]
-            if (b < tile.count && half == 0) {
+            __syncthreads();  // the other parts' populations are in hand[]
+            if (b < tile.count && part == 0) {
                 const int64_t p = tile.begin + b;
                 f[0] = a.fin[p];
                 if (!own) {
                     interp_nearest<T, B>(a, tile, b, reinterpret_cast<const T *>(sh), f);
-                } else if constexpr (kSplit) {
-    #pragma unroll
-                    for (int q = 0; q < NQ; ++q) vunpack(f + 1 + (NQ + q) * W, hand[b * NQ + q]);
+                } else {
+#pragma unroll
+                    for (int q = NQ; q < NV; ++q) vunpack(f + 1 + q * W, hand[b * NV + q]);
                 }
                 // 3. wall bounce-back: unknown populations take the streamed opposite population
                 if (a.mask) {
                     const uint16_t mb = a.mask[p];
                     if (mb) {
                         T g[9];
-    #pragma unroll
+#pragma unroll
                         for (int k = 0; k < 9; ++k) g[k] = f[k];
-    #pragma unroll
+#pragma unroll
                         for (int k = 1; k < 9; ++k)
                             if (mb >> k & 1u) f[k] = g[opp_of(k)];
                     }
@@ -266,7 +263,7 @@ __global__ void __launch_bounds__(step_threads(B), step_min_blocks(B, (int)sizeo
                 else
                     collide<T>(f, T(0), inv_tau, gx, gy, rho, ux, uy);
                 // 5. store
-    #pragma unroll
+#pragma unroll
                 for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
                 if (a.mom) {
                     a.mom[p] = rho;
@@ -509,7 +506,7 @@ int check_dtype(const mlbm_weights *w, int dtype) {
 
 template <typename T>
 size_t step_smem(const mlbm_weights *w) {
-    const size_t hand = w->tile_nodes == kTileNodesTiny ? (size_t)kTileNodesTiny * 4 * sizeof(T) : 0;
+    const size_t hand = w->tile_nodes == kTileNodesTiny ? (size_t)kTileNodesTiny * 8 * sizeof(T) : 0;
     return (size_t)w->umax * 8 * sizeof(T) + hand;
 }
 
@@ -533,7 +530,7 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     const size_t smem = step_smem<T>(w);
     return with_tile_nodes(w->tile_nodes, [&](auto Bc) {
         constexpr int B = decltype(Bc)::value;
-        step_kernel<T, B><<<grid, step_threads(B), smem, st>>>(a);
+        step_kernel<T, B><<<grid, step_threads(B, (int)sizeof(T)), smem, st>>>(a);
         return cuda_check_step(cudaGetLastError(), "step_kernel launch");
     });
 }
@@ -558,7 +555,7 @@ int prepare_step_grids(mlbm_weights *w) {
                                  "step shared-memory attribute");
         if (rc) return rc;
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], step_threads(w->tile_nodes), sm[i]);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], step_threads(w->tile_nodes, i == 0 ? 4 : 8), sm[i]);
         w->step_grid[i] = std::max(1, std::min(w->ntiles, std::max(1, per_sm) * w->num_sms));
     }
     return MLBM_OK;
