@@ -362,7 +362,9 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
             const int L = a.slen[ws];
             const int64_t q0 = a.sbeg[ws] + (b & 31);
             const uint16_t *__restrict__ sp = a.slot + q0;
-            const VT *__restrict__ cp = reinterpret_cast<const VT *>(a.coef) + q0 * NV;
+            // coefficients in planes per 32-entry row of the slice: vector q of entry (e, lane)
+            // at (sbeg + 32 e) NV + 32 q + lane, so each warp load is 512 contiguous bytes
+            const VT *__restrict__ cp = reinterpret_cast<const VT *>(a.coef) + a.sbeg[ws] * NV + (b & 31);
             VT acc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) vzero(acc[q]);
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
                 for (int r = 0; r < 4; ++r) {
                     sl[r] = sp[(int64_t)32 * (e + r)];
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) c[r][q] = __ldcs(cp + ((int64_t)32 * (e + r)) * NV + q);
+                    for (int q = 0; q < NV; ++q) c[r][q] = __ldcs(cp + ((int64_t)32 * (e + r)) * NV + 32 * q);
                 }
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
             for (; e < L; ++e) {
                 const int s0 = sp[(int64_t)32 * e];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) vfma_acc(acc[q], __ldcs(cp + ((int64_t)32 * e) * NV + q), sh[s0 * NV + q]);
+                for (int q = 0; q < NV; ++q) vfma_acc(acc[q], __ldcs(cp + ((int64_t)32 * e) * NV + 32 * q), sh[s0 * NV + q]);
             }
             T v[8];
 #pragma unroll
@@ -425,7 +427,7 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
         const int64_t m = tile.begin + (row ? rowp[g] : 0);
         const int32_t e0 = row ? csr_ptr[m] : 0, e1 = row ? csr_ptr[m + 1] : 0;
         for (int e = 0; e < L; ++e) {
-            const int64_t q = sbeg[ws] + (b & 31) + (int64_t)32 * e;
+            const int64_t qb = sbeg[ws] + (int64_t)32 * e;  // first entry of the slice's row e
             T v[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = T(0);
@@ -444,8 +446,10 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
                     }
                 }
             }
+            // planes: vector h (directions h W .. h W + W - 1) of lane b % 32 at (qb NV + 32 h + lane) W
+            constexpr int W = V<T>::width, NV = 8 / W;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) coef[q * 8 + k] = v[k];
+            for (int k = 0; k < 8; ++k) coef[(qb * NV + 32 * (k / W) + (b & 31)) * W + k % W] = v[k];
         }
     }
 }
