@@ -98,9 +98,12 @@ def test_gpu_weights_reproduce_polynomials(K, deg):
 
 # ----------------------------------------------------------------------------- FP64 step
 
-@pytest.mark.parametrize("n_side,K,deg,ratio", [(32, 12, 2, 1.0), (20, 30, 4, 1.0), (17, 16, 3, 0.5)])
+@pytest.mark.parametrize("n_side,K,deg,ratio", [(32, 12, 2, 1.0), (20, 30, 4, 1.0), (17, 16, 3, 0.5),
+                                                 (200, 12, 2, 1.0)])
 def test_fp64_step_matches_oracle_per_step(n_side, K, deg, ratio):
-    """Shared (oracle) shape vectors uploaded to the GPU: every step agrees to 1e-12."""
+    """Shared (oracle) shape vectors uploaded to the GPU: every step agrees to 1e-12.  The
+    small clouds run the one-warp tiles (several threads per node), 200^2 nodes the 128-node
+    tiles."""
     xy, dx, cloud, w = _setup_tgv(n_side, K, deg, ratio=ratio)
     sidx, W = _upload_oracle_weights(w, xy, K, deg, dx)
     tau = 0.8
