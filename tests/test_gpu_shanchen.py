@@ -65,10 +65,12 @@ def test_no_interaction_is_the_plain_step(dtype):
     assert torch.equal(b, c) and torch.equal(mb, mc)
 
 
-def test_fp64_steps_match_the_oracle_step_by_step():
+@pytest.mark.parametrize("n_side,K,deg,steps", [(24, 16, 3, 20), (200, 12, 2, 4)])
+def test_fp64_steps_match_the_oracle_step_by_step(n_side, K, deg, steps):
     """Oracle shape vectors uploaded; the state after every step is the oracle's Shan-Chen
-    post-collision state to 1e-12 relative, and the moments are those of the streamed state."""
-    n_side, K, deg, tau, G = 24, 16, 3, 1.0, -5.0
+    post-collision state to 1e-12 relative, and the moments are those of the streamed state.
+    24^2 nodes run one-warp tiles, 200^2 the 128-node tiles."""
+    tau, G = 1.0, -5.0
     dx = 0.5 / n_side
     xy = mi.jittered_lattice(n_side, 0.3, seed=32)
     cloud, w = _periodic(xy, K, deg, dx)
@@ -83,7 +85,7 @@ def test_fp64_steps_match_the_oracle_step_by_step():
     mom = torch.empty(3 * n, dtype=torch.float64, device=DEV)
     st = oracle.ScStepper(sidx, W, tau, G)
     params = [(tau, 0.0, 1.0)]
-    for it in range(20):
+    for it in range(steps):
         mlbm.sc_step(w, params, (G, 1.0), mlbm.F64, a, b, mom)
         a, b = b, a
         f = st.step(f)
