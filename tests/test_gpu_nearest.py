@@ -39,11 +39,13 @@ def test_nearest_weights_and_departure_nodes_match_oracle(n_side, K, deg, ratio)
     assert err <= {2: 1e-9, 4: 1e-7}[deg], err
 
 
-@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", None)])
-def test_nearest_step_matches_oracle(dtype, tol):
+@pytest.mark.parametrize("dtype,tol,n_side,K,deg,steps", [("f64", 1e-12, 24, 16, 3, 60), ("f32", None, 24, 16, 3, 60),
+                                                        ("f64", 1e-12, 200, 9, 1, 20)])
+def test_nearest_step_matches_oracle(dtype, tol, n_side, K, deg, steps):
     """Oracle shape vectors uploaded; FP64 agrees per step to 1e-12, FP32 within 1e-6 relative
-    L2 of the velocity after the run (dx_ml = 2 h: departure points beyond the own stencil)."""
-    n_side, K, deg, dx, tau = 24, 16, 3, 2.0 / 24, 0.8
+    L2 of the velocity after the run (dx_ml = 2 h: departure points beyond the own stencil).
+    24^2 nodes run one-warp tiles, 200^2 the 128-node tiles."""
+    dx, tau = 2.0 / n_side, 0.8
     xy, cloud, w = _periodic_nearest(n_side, K, deg, dx, seed=8)
     sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode="paper")
     w.upload(W[1:], oracle.stencils(xy, K, box=(1.0, 1.0)).astype(np.int32))
@@ -56,7 +58,6 @@ def test_nearest_step_matches_oracle(dtype, tol):
     b = torch.empty_like(a)
     mlbm.init(w, params, dt, _t(rho), _t(u), _t(v), a)
     perm = cloud.perm()
-    steps = 60
     for it in range(steps):
         mlbm.step(w, params, dt, a, b)
         a, b = b, a
