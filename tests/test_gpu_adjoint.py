@@ -262,12 +262,14 @@ def test_fp32_adjoint_step_close_to_fp64_and_deterministic(from_next):
     np.testing.assert_allclose(out[mlbm.F32][1].cpu().numpy(), out[mlbm.F64][1].cpu().numpy(), rtol=1e-4)
 
 
+@pytest.mark.parametrize("n_side", [200, 600])
 @pytest.mark.parametrize("from_next", [False, True], ids=["recompute", "from_next"])
-def test_adjoint_step_large_tiles_matches_finite_differences(from_next):
-    """A cloud large enough for 512-node tiles (360k nodes): the tiled reverse step against
-    central differences of the forward."""
-    xy = mi.jittered_lattice(600, 0.3, seed=12)
-    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=12, degree=2, dx_ml=1.0 / 600))
+def test_adjoint_step_large_tiles_matches_finite_differences(from_next, n_side):
+    """Clouds large enough for 128-node tiles (40k nodes) and 512-node tiles (360k nodes): the
+    tiled reverse step against central differences of the forward."""
+    xy = mi.jittered_lattice(n_side, 0.3, seed=12)
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=12, degree=2,
+                                      dx_ml=1.0 / n_side))
     w = mlbm.build_weights(cloud)
     params = [(0.8, 1e-5, 1.0)]
     s = _rand_state(w, params, xy, seed=13)
