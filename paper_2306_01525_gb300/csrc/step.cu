@@ -2,11 +2,12 @@
 // as a pull; Sec. 2.3 semi-Lagrangian streaming; Sec. 3 forcing and wall bounce-back),
 // initial state, moments, norms and the CUDA-graph step loop.
 //
-// Step kernel: persistent CTAs walk a tile table (tiles = runs of <= 256 stored nodes of one
-// segment, largest stencils first), one thread per node.  For node i the stencil index idx[j][i]
-// is loaded once and reused by all eight moving directions; shape vectors are [dir][j][node] SoA
-// so every warp load of a weight is one fully used 128-byte line; the gathered f^post values
-// hit L1/L2 because the nodes are Morton ordered.
+// Step kernel: persistent CTAs walk a tile table (tiles = runs of 512, 128 or 32 stored nodes of
+// one segment, largest stencils first), one thread per node (one per 16-byte direction vector
+// in 32-node tiles).  A tile's halo of f^post is staged in shared memory; for node i each stencil
+// member's 16-bit halo slot is loaded once and reused by all eight moving directions, and the
+// shape vectors are stored per tile as [member][direction vector][node] so that every warp load
+// is a contiguous 512-byte run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
