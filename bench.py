@@ -155,10 +155,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_oracle_gnups(seconds: float, steps=None, warmup: int = 0):
-    """Time the FP64 CPU oracle's step on the bounded sample cloud (all host cores)."""
+def cpu_oracle_gnups(seconds: float, steps=None, warmup: int = 0, threads=None):
+    """Time the FP64 CPU oracle's step on the bounded sample cloud (all host cores, or the given
+    number of threads)."""
     import mlbm_inputs as mi
     import oracle
+
+    all_threads = oracle.num_threads()
+    if threads:
+        oracle.set_threads(threads)
 
     c = CPU_SAMPLE
     xy = mi.jittered_lattice(c["n_side"], 0.3, seed=c["seed"])
@@ -177,7 +182,10 @@ def cpu_oracle_gnups(seconds: float, steps=None, warmup: int = 0):
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (steps is None and el >= seconds and done >= 3):
             break
-    return dict(value=n * done / el / 1e9, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+    cores = oracle.num_threads()
+    if threads:
+        oracle.set_threads(all_threads)
+    return dict(value=n * done / el / 1e9, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"FP64 oracle step on a {c['n_side']}x{c['n_side']} jittered cloud of the "
                        f"same recipe (N_L={c['K']}, degree {c['deg']}), {done} steps, "
                        f"{el:.1f} s"), done, el
@@ -809,6 +817,8 @@ def run_mlbm(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_gnups(args.cpu_seconds)
+        one, _, _ = cpu_oracle_gnups(4.0, threads=1)
+        cpu["single_thread"] = {"value": one["value"], "unit": UNIT, "cores": one["cores"], "sample": one["sample"]}
     extras = {}
     t_cloud_host = None
     if world == 1 and not args.no_extras:
