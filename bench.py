@@ -423,7 +423,7 @@ def bench_adjoint(steps: int = 2000):
     gbs = bpn * n / (rev_us * 1e-6) / 1e9
     return {"workload": "annulus_250k_k24_d3_adjoint", "nodes": n, "steps": steps, "dtype": "f32",
             "checkpoint_every": int(np.ceil(np.sqrt(steps))), "forward_s": t_fwd,
-            "forward_backward_s": t_all, "loss": float(loss),
+            "forward_backward_s": t_all, "loss": float(loss.detach()),
             "dloss_dtau": float(tt.grad), "dloss_dg": float(gt.grad),
             "dloss_du0_norm": float(a0.grad.norm()),
             "peak_torch_mem_gb": peak_mem,
