@@ -324,9 +324,10 @@ __device__ __forceinline__ void vfma_acc(double2 &acc, const double2 w, const do
 //      lam_prev_k(m), k = 1..8.  c_kj is the coefficient of s_k(s_j(i)) in the forward's
 //      fhat_k(i): W_k[j](i), except the centre of the FP32 difference form, 1 - sum_{j>=1}
 //      W_k[j](i).  The entries are sliced by 32 rows (entry e of the slice's lane l at
-//      sbeg + 32 e + l, rows padded to the slice's longest with zero coefficients), so a warp
-//      streams 32 consecutive entries per pass, and the gathered cotangents come from shared
-//      memory.  No atomics: deterministic.
+//      sbeg + 32 e + l, rows padded to the slice's longest with slot 0 and zero coefficients;
+//      the coefficients in planes, vector q of the 32 lanes' entries contiguous), so every
+//      warp load is a contiguous run, and the gathered cotangents come from shared memory.
+//      No atomics: deterministic.
 template <typename T, int B, bool kFromNext>
 __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
     using VT = typename V<T>::type;
