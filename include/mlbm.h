@@ -238,6 +238,20 @@ int mlbm_step(const mlbm_weights *w, const mlbm_params *params, int dtype, const
 int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
              int64_t nsteps, void *stream);
 
+/* Each segment run for its own number of steps in one call (the batched convergence sweep,
+ * whose runs end at different times, e.g. the paper's end time of each resolution, Sec. 3).
+ *   seg_steps  host, nseg int64 >= 0: steps of each segment.
+ * The call makes S = max(seg_steps) steps ping-ponging between f_a and f_b as mlbm_run does,
+ * each step over the tiles of the segments not yet done (in CUDA graphs per run of steps with
+ * the same active segments), and then copies the final state of every segment whose count
+ * has the other parity than S into the result buffer: the result (every segment after its
+ * own number of steps) is in f_a when S is even, else in f_b.  Finished segments are not
+ * touched otherwise, so each segment's result equals a run of that segment alone.  The other
+ * buffer holds scratch.  Calls on one weights object must not run concurrently.
+ * Errors: MLBM_EINVAL (NULL, f_a == f_b, negative count), MLBM_ENOMEM, MLBM_ECUDA. */
+int mlbm_run_until(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
+                   const int64_t *seg_steps, void *stream);
+
 /* ---------------------------------------------------------------------------------------
  * mlbm_step_host -- one time step (as mlbm_step) for each of nbatch independent states held
  * in HOST memory, end to end: state b is copied to the device, stepped, and its new

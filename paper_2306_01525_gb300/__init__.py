@@ -28,7 +28,7 @@ __all__ = [
     "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "STENCIL_OWN", "STENCIL_NEAREST",
     "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
-    "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
+    "run_until", "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
     "lattice_init", "lattice_step", "step_host", "sc_step",
 ]
 
@@ -95,6 +95,7 @@ def lib():
             L.mlbm_init.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_run.argtypes = [_vp, _vp, _c_int, _vp, _vp, _c_i64, _vp]
+            L.mlbm_run_until.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_step_host.argtypes = [_vp, _vp, _c_int, _c_i64, _vp, _vp, _vp]
             L.mlbm_sc_step.argtypes = [_vp, _vp, _vp, _c_int, _vp, _vp, _vp, _vp]
             L.mlbm_moments.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
@@ -371,6 +372,18 @@ def run(w: Weights, params, dtype, f_a, f_b, nsteps: int, stream=None):
                           _state(w, dtype, f_a, "f_a"), _state(w, dtype, f_b, "f_b"),
                           int(nsteps), _stream(stream)))
     return f_a if nsteps % 2 == 0 else f_b
+
+
+def run_until(w: Weights, params, dtype, f_a, f_b, seg_steps, stream=None):
+    """Every segment after its own number of steps seg_steps[s]; returns the tensor holding
+    the result (f_a when max(seg_steps) is even, else f_b; the other one is scratch)."""
+    steps = np.ascontiguousarray(np.asarray(seg_steps, dtype=np.int64).reshape(-1))
+    if steps.size != w.nseg:
+        raise ValueError(f"seg_steps needs {w.nseg} entries")
+    _check(lib().mlbm_run_until(w.handle, _params(params, w.nseg), dtype,
+                                _state(w, dtype, f_a, "f_a"), _state(w, dtype, f_b, "f_b"),
+                                steps.ctypes.data, _stream(stream)))
+    return f_a if int(steps.max(initial=0)) % 2 == 0 else f_b
 
 
 def moments(w: Weights, params, dtype, f, rho=None, ux=None, uy=None, stream=None):

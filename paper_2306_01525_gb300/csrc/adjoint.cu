@@ -732,8 +732,7 @@ template <typename T, int B>
 int launch_adj_local(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
     const size_t smem = (size_t)w->umax * 8 * sizeof(T);
     const void *fn = (const void *)adj_local_kernel<T, B>;
-    int rc = cuda_check_step(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                             "adjoint shared memory");
+    int rc = allow_dynamic_smem(fn);
     if (rc) return rc;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, smem);
@@ -747,8 +746,7 @@ template <typename T, int B, bool kFromNext>
 int launch_adj_pull(mlbm_weights *w, const AdjArgs<T> &a, cudaStream_t st) {
     const size_t smem = (size_t)w->adj_rmax * 8 * sizeof(T);
     const void *fn = (const void *)adj_pull_kernel<T, B, kFromNext>;
-    int rc = cuda_check_step(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                             "adjoint shared memory");
+    int rc = allow_dynamic_smem(fn);
     if (rc) return rc;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, B, smem);

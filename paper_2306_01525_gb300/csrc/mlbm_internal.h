@@ -86,6 +86,12 @@ inline int choose_tile_nodes(const std::vector<int64_t> &seg_nodes, int num_sms)
     return kTileNodesTiny;
 }
 
+// Let kernel fn use up to the device's opt-in maximum of dynamic shared memory.  The attribute
+// belongs to the function, not to a weights object: setting it to one object's own need would
+// lower it under another object's launches (and under graphs captured for them), so every
+// launcher that needs more than the default sets it to the maximum.  Defined in step.cu.
+int allow_dynamic_smem(const void *fn);
+
 // f(std::integral_constant<int, B>{}) for the tile size B of the weights (kernel dispatch).
 template <typename F>
 int with_tile_nodes(int tile_nodes, F &&f) {
@@ -118,8 +124,11 @@ struct GraphKey {
     int dtype;
     int64_t chunk;
     std::vector<double> params;
+    const void *tiles = nullptr;  // tile table the captured steps walk, and its length
+    int64_t ntiles = 0;
     bool operator<(const GraphKey &o) const {
-        return std::tie(a, b, dtype, chunk, params) < std::tie(o.a, o.b, o.dtype, o.chunk, o.params);
+        return std::tie(a, b, dtype, chunk, params, tiles, ntiles) <
+               std::tie(o.a, o.b, o.dtype, o.chunk, o.params, o.tiles, o.ntiles);
     }
 };
 
@@ -169,6 +178,10 @@ struct mlbm_weights_impl {
     int64_t nsys = 0;
     int device = 0;
     std::map<GraphKey, void *> graphs;  // cudaGraphExec_t
+    // mlbm_run_until: host copy of the tile table, and a device table re-sorted per call by the
+    // segments' step counts (longest first), so the active tiles of any step are a prefix
+    std::vector<TileDev> tiles_host;
+    TileDev *d_tiles_run = nullptr;
     // adjoint, built on first use: per forward tile its rows ordered by transposed-stencil
     // length ([ntiles][B] offsets), its reverse halo (own nodes, then every other node that reads
     // one of them, sorted; offset and size per tile), per 32-row slice of that order its first

@@ -228,11 +228,8 @@ int launch_sc_t(mlbm_weights *w, const ScArgs<T> &a, cudaStream_t st) {
     const size_t sm1 = (size_t)w->umax * 8 * sizeof(T), sm2 = (size_t)w->umax * sizeof(T);
     if (sm1 > (size_t)maxsm) return fail(MLBM_EINVAL, "a tile's halo does not fit in shared memory at this precision");
     const void *k1 = (const void *)sc_stream_kernel<T, B>, *k2 = (const void *)sc_collide_kernel<T, B>;
-    int rc = cuda_check_step(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1),
-                             "Shan-Chen shared memory");
-    if (!rc)
-        rc = cuda_check_step(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2),
-                             "Shan-Chen shared memory");
+    int rc = allow_dynamic_smem(k1);
+    if (!rc) rc = allow_dynamic_smem(k2);
     if (rc) return rc;
     int per1 = 0, per2 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k1, B, sm1);

@@ -28,6 +28,21 @@ int cuda_check_step(cudaError_t e, const char *what) {
     return fail(MLBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+int allow_dynamic_smem(const void *fn) {
+    int dev = 0, maxsm = 0;
+    cudaFuncAttributes fa;
+    int rc = cuda_check_step(cudaGetDevice(&dev), "current device");
+    if (!rc) rc = cuda_check_step(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev),
+                                  "shared-memory limit");
+    if (!rc) rc = cuda_check_step(cudaFuncGetAttributes(&fa, fn), "kernel attributes");
+    // the dynamic part may use what the kernel's static shared memory leaves of the maximum
+    if (!rc)
+        rc = cuda_check_step(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  maxsm - (int)fa.sharedSizeBytes),
+                             "shared-memory attribute");
+    return rc;
+}
+
 namespace {
 
 template <typename T>
@@ -512,9 +527,10 @@ size_t step_smem(const mlbm_weights *w) {
 }
 
 template <typename T>
-int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom, cudaStream_t st) {
+int launch_step_t(const mlbm_weights *w, const TileDev *tiles, int ntiles, const void *fin, void *fout, void *mom,
+                  cudaStream_t st) {
     StepArgs<T> a;
-    a.tiles = w->d_tiles;
+    a.tiles = tiles;
     a.halo = w->d_halo;
     a.lidx = w->d_lidx;
     a.wt = std::is_same<T, float>::value ? (const T *)w->d_w32t : (const T *)w->d_w64t;
@@ -525,9 +541,9 @@ int launch_step_t(const mlbm_weights *w, const void *fin, void *fout, void *mom,
     a.fout = (T *)fout;
     a.mom = (T *)mom;
     a.N = w->N;
-    a.ntiles = w->ntiles;
+    a.ntiles = ntiles;
     a.umax = w->umax;
-    const int grid = w->step_grid[std::is_same<T, float>::value ? 0 : 1];
+    const int grid = std::max(1, std::min(ntiles, w->step_grid[std::is_same<T, float>::value ? 0 : 1]));
     const size_t smem = step_smem<T>(w);
     return with_tile_nodes(w->tile_nodes, [&](auto Bc) {
         constexpr int B = decltype(Bc)::value;
@@ -552,8 +568,7 @@ int prepare_step_grids(mlbm_weights *w) {
     for (int i = 0; i < 2; ++i) {
         w->step_grid[i] = 0;
         if (sm[i] > (size_t)maxsm) continue;
-        int rc = cuda_check_step(cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[i]),
-                                 "step shared-memory attribute");
+        int rc = allow_dynamic_smem(fns[i]);
         if (rc) return rc;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], step_threads(w->tile_nodes, i == 0 ? 4 : 8), sm[i]);
@@ -562,9 +577,15 @@ int prepare_step_grids(mlbm_weights *w) {
     return MLBM_OK;
 }
 
+// One step over the first ntiles tiles of a tile table (the weights' own, or a re-sorted copy).
+int launch_step_tiles(const mlbm_weights *w, int dtype, const TileDev *tiles, int ntiles, const void *fin,
+                      void *fout, void *mom, cudaStream_t st) {
+    return dtype == MLBM_F32 ? launch_step_t<float>(w, tiles, ntiles, fin, fout, mom, st)
+                             : launch_step_t<double>(w, tiles, ntiles, fin, fout, mom, st);
+}
+
 int launch_step(const mlbm_weights *w, int dtype, const void *fin, void *fout, void *mom, cudaStream_t st) {
-    return dtype == MLBM_F32 ? launch_step_t<float>(w, fin, fout, mom, st)
-                             : launch_step_t<double>(w, fin, fout, mom, st);
+    return launch_step_tiles(w, dtype, w->d_tiles, w->ntiles, fin, fout, mom, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -648,20 +669,21 @@ int mlbm_step(const mlbm_weights *w, const mlbm_params *params, int dtype, const
     return launch_step(w, dtype, f_in, f_out, moments, st);
 }
 
-int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
-             int64_t nsteps, void *stream) {
-    set_error("");
-    if (!w || !f_a || !f_b) return fail(MLBM_EINVAL, "NULL argument");
-    if (f_a == f_b) return fail(MLBM_EINVAL, "f_a and f_b must differ");
-    if (nsteps < 0) return fail(MLBM_EINVAL, "nsteps < 0");
-    int rc = check_dtype(w, dtype);
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    if ((rc = set_params(w, params, st))) return rc;
+}  // extern "C"
+
+namespace mlbm {
+namespace {
+
+// nsteps steps ping-ponging f_a -> f_b -> f_a ... over the first ntiles tiles of a tile table:
+// 64-step CUDA graphs (cached per buffers, dtype and tile table prefix) and the remainder as
+// single launches.
+int run_steps(mlbm_weights *w, int dtype, const TileDev *tiles, int ntiles, void *f_a, void *f_b, int64_t nsteps,
+              cudaStream_t st) {
+    int rc = MLBM_OK;
     const int64_t G = 64;  // steps per captured graph (even: the graph maps f_a back to f_a)
     int64_t reps = nsteps / G, rem = nsteps % G;
     if (reps > 0) {
-        GraphKey key{f_a, f_b, dtype, G, {}};
+        GraphKey key{f_a, f_b, dtype, G, {}, tiles, ntiles};
         cudaGraphExec_t exec = nullptr;
         auto it = w->graphs.find(key);
         if (it != w->graphs.end()) {
@@ -672,7 +694,7 @@ int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, v
                 return rc;
             rc = cuda_check_step(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
             for (int64_t i = 0; i < G && !rc; ++i)
-                rc = launch_step(w, dtype, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, cs);
+                rc = launch_step_tiles(w, dtype, tiles, ntiles, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, cs);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(cs, &graph);
             if (!rc) rc = cuda_check_step(e, "end capture");
@@ -686,7 +708,94 @@ int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, v
             if ((rc = cuda_check_step(cudaGraphLaunch(exec, st), "graph launch"))) return rc;
     }
     for (int64_t i = 0; i < rem; ++i)
-        if ((rc = launch_step(w, dtype, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, st))) return rc;
+        if ((rc = launch_step_tiles(w, dtype, tiles, ntiles, (i & 1) ? f_b : f_a, (i & 1) ? f_a : f_b, nullptr, st)))
+            return rc;
+    return MLBM_OK;
+}
+
+}  // namespace
+}  // namespace mlbm
+
+extern "C" {
+
+int mlbm_run(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
+             int64_t nsteps, void *stream) {
+    set_error("");
+    if (!w || !f_a || !f_b) return fail(MLBM_EINVAL, "NULL argument");
+    if (f_a == f_b) return fail(MLBM_EINVAL, "f_a and f_b must differ");
+    if (nsteps < 0) return fail(MLBM_EINVAL, "nsteps < 0");
+    int rc = check_dtype(w, dtype);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = set_params(w, params, st))) return rc;
+    return run_steps(w, dtype, w->d_tiles, w->ntiles, f_a, f_b, nsteps, st);
+}
+
+int mlbm_run_until(mlbm_weights *w, const mlbm_params *params, int dtype, void *f_a, void *f_b,
+                   const int64_t *seg_steps, void *stream) {
+    set_error("");
+    if (!w || !f_a || !f_b || !seg_steps) return fail(MLBM_EINVAL, "NULL argument");
+    if (f_a == f_b) return fail(MLBM_EINVAL, "f_a and f_b must differ");
+    int64_t S = 0;
+    for (int s = 0; s < w->nseg; ++s) {
+        if (seg_steps[s] < 0) return fail(MLBM_EINVAL, "negative step count");
+        S = std::max(S, seg_steps[s]);
+    }
+    int rc = check_dtype(w, dtype);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = set_params(w, params, st))) return rc;
+    if (S == 0) return MLBM_OK;
+    // the tile table sorted by the segments' step counts, longest first (stable: within a count
+    // the weights' own order, largest stencils first), so each step's active tiles are a prefix
+    if (w->tiles_host.empty()) {
+        w->tiles_host.resize((size_t)w->ntiles);
+        if ((rc = cuda_check_step(cudaMemcpy(w->tiles_host.data(), w->d_tiles, sizeof(TileDev) * w->ntiles,
+                                             cudaMemcpyDeviceToHost), "tile table")))
+            return rc;
+        if (cudaMalloc(&w->d_tiles_run, sizeof(TileDev) * w->ntiles) != cudaSuccess) {
+            cudaGetLastError();
+            w->d_tiles_run = nullptr;
+            w->tiles_host.clear();
+            return fail(MLBM_ENOMEM, "tile table allocation failed");
+        }
+    }
+    std::vector<TileDev> sorted(w->tiles_host);
+    std::stable_sort(sorted.begin(), sorted.end(), [&](const TileDev &p, const TileDev &q) {
+        return seg_steps[p.seg] > seg_steps[q.seg];
+    });
+    // stream-ordered: earlier steps still reading the table finish before it changes
+    if ((rc = cuda_check_step(cudaMemcpyAsync(w->d_tiles_run, sorted.data(), sizeof(TileDev) * sorted.size(),
+                                              cudaMemcpyHostToDevice, st), "tile table")) ||
+        (rc = cuda_check_step(cudaStreamSynchronize(st), "tile table")))
+        return rc;
+    // intervals between the distinct step counts: steps done .. v - 1 run the tiles of the
+    // segments with at least v steps
+    std::vector<int64_t> ends;
+    for (int s = 0; s < w->nseg; ++s)
+        if (seg_steps[s] > 0) ends.push_back(seg_steps[s]);
+    std::sort(ends.begin(), ends.end());
+    ends.erase(std::unique(ends.begin(), ends.end()), ends.end());
+    int64_t done = 0;
+    for (int64_t v : ends) {
+        int active = 0;
+        while (active < w->ntiles && seg_steps[sorted[active].seg] >= v) ++active;
+        void *cur = (done & 1) ? f_b : f_a, *oth = (done & 1) ? f_a : f_b;
+        if ((rc = run_steps(w, dtype, w->d_tiles_run, active, cur, oth, v - done, st))) return rc;
+        done = v;
+    }
+    // a segment that stopped at a step count of the other parity left its state in the other
+    // buffer: copy its rows of the nine populations over
+    const size_t es = dtype == MLBM_F32 ? sizeof(float) : sizeof(double);
+    char *res = (char *)((S & 1) ? f_b : f_a), *other = (char *)((S & 1) ? f_a : f_b);
+    for (int s = 0; s < w->nseg; ++s) {
+        if (((S - seg_steps[s]) & 1) == 0) continue;
+        const SegmentHost &h = w->seg[s];
+        if ((rc = cuda_check_step(cudaMemcpy2DAsync(res + h.off * es, w->N * es, other + h.off * es, w->N * es,
+                                                    h.n * es, 9, cudaMemcpyDeviceToDevice, st),
+                                  "segment state copy")))
+            return rc;
+    }
     return MLBM_OK;
 }
 

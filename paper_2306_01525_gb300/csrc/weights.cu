@@ -408,6 +408,7 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_params);
     cudaFree(w->d_sc);
     cudaFree(w->d_sc_psi);
+    cudaFree(w->d_tiles_run);
     cudaFree(w->d_adj_rowp);
     cudaFree(w->d_adj_rhalo);
     cudaFree(w->d_adj_roff);
@@ -450,8 +451,7 @@ static int launch_solve(mlbm_weights *w, const double *d_x, const double *d_y, u
                         int64_t count, int wpb, cudaStream_t st) {
     const SolveShape sh = solve_shape(w);
     const size_t smem = (size_t)wpb * sh.slot * sizeof(double);
-    int rc = cuda_check(cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
-                        "cudaFuncSetAttribute(solve)");
+    int rc = allow_dynamic_smem((const void *)solve_kernel);
     if (rc) return rc;
     SolveArgs a;
     a.seg = w->d_seg;

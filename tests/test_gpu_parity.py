@@ -282,6 +282,65 @@ def test_batched_segments_match_single_runs_and_oracle():
         assert err <= 1e-7, (s, err)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_run_until_gives_each_segment_its_own_run(dtype):
+    """Segments of uneven size, stencil, degree and tau, each run for its own number of steps in
+    one call (even, odd, zero, past a 64-step graph): every segment's result equals a run of
+    that segment alone, bit for bit."""
+    dt = mlbm.F32 if dtype == "f32" else mlbm.F64
+    cases = [(16, 12, 2, 1.0, 0.8, 37), (20, 16, 3, 0.5, 0.7, 0), (12, 24, 4, 0.25, 1.1, 150),
+             (9, 8, 1, 1.0, 0.9, 64)]
+    parts, segs, params, steps = [], [], [], []
+    for s_, (ns, K, deg, ratio, tau, n) in enumerate(cases):
+        parts.append(mi.jittered_lattice(ns, 0.3, seed=80 + s_))
+        segs.append(_periodic(K, deg, ratio / ns))
+        params.append((tau, 0.0, 1.0))
+        steps.append(n)
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    w = mlbm.build_weights(mlbm.build_cloud(xy, segs, offs))
+    u = np.concatenate([mi.tgv_initial(p, 0.01)[1] for p in parts])
+    v = np.concatenate([mi.tgv_initial(p, 0.01)[2] for p in parts])
+    fa = _gpu_init(w, params, dt, np.ones(xy.shape[1]), u, v)
+    fb = torch.empty_like(fa)
+    res = mlbm.run_until(w, params, dt, fa, fb, steps)
+    assert res is (fb if max(steps) % 2 else fa)
+    rb, ub, vb = (t.cpu().numpy() for t in mlbm.moments(w, params, dt, res))
+    for s_, p in enumerate(parts):
+        w1 = mlbm.build_weights(mlbm.build_cloud(p, segs[s_]))
+        _, u1, v1 = mi.tgv_initial(p, 0.01)
+        f1 = _gpu_init(w1, [params[s_]], dt, np.ones(p.shape[1]), u1, v1)
+        r1 = mlbm.run(w1, [params[s_]], dt, f1, torch.empty_like(f1), steps[s_])
+        ro, uo, vo = (t.cpu().numpy() for t in mlbm.moments(w1, [params[s_]], dt, r1))
+        sl = slice(offs[s_], offs[s_ + 1])
+        np.testing.assert_array_equal(rb[sl], ro)
+        np.testing.assert_array_equal(ub[sl], uo)
+        np.testing.assert_array_equal(vb[sl], vo)
+    # equal counts: the same as one mlbm_run of the whole cloud
+    ga = _gpu_init(w, params, dt, np.ones(xy.shape[1]), u, v)
+    gb = torch.empty_like(ga)
+    ha = ga.clone()
+    r_all = mlbm.run(w, params, dt, ga, gb, 71)
+    r_until = mlbm.run_until(w, params, dt, ha, torch.empty_like(ha), [71] * len(cases))
+    assert torch.equal(r_all, r_until)
+
+
+def test_weights_objects_with_smaller_halos_leave_earlier_ones_usable():
+    """Building weights whose tiles need less shared memory must not shrink what the kernels of
+    an existing weights object (and the graphs captured for it) may use."""
+    xy, dx, cloud, w = _setup_tgv(24, 30, 4)
+    params = [(0.8, 0.0, 1.0)]
+    rho, u, v = mi.tgv_initial(xy, 0.01)
+    for dtype in (mlbm.F32, mlbm.F64):
+        fa = _gpu_init(w, params, dtype, rho, u, v)
+        ref = mlbm.run(w, params, dtype, fa.clone(), torch.empty_like(fa), 70).clone()
+        small = mlbm.build_weights(mlbm.build_cloud(mi.jittered_lattice(8, 0.3, seed=2), _periodic(6, 1, 1.0 / 8)))
+        assert small.n == 64
+        got = mlbm.run(w, params, dtype, fa.clone(), torch.empty_like(fa), 70)
+        assert torch.equal(got, ref)
+        del small
+
+
 def test_run_graph_equals_repeated_steps():
     xy, dx, cloud, w = _setup_tgv(24, 12, 2)
     params = [(0.8, 0.0, 1.0)]
