@@ -323,6 +323,17 @@ def test_run_until_gives_each_segment_its_own_run(dtype):
     r_all = mlbm.run(w, params, dt, ga, gb, 71)
     r_until = mlbm.run_until(w, params, dt, ha, torch.empty_like(ha), [71] * len(cases))
     assert torch.equal(r_all, r_until)
+    # no steps at all: the state stays where it is, the other buffer is not written
+    za = _gpu_init(w, params, dt, np.ones(xy.shape[1]), u, v)
+    keep = za.clone()
+    zb = torch.full_like(za, 3.0)
+    assert mlbm.run_until(w, params, dt, za, zb, [0] * len(cases)) is za
+    assert torch.equal(za, keep) and bool((zb == 3.0).all())
+    with pytest.raises(mlbm.MLBMError) as e:
+        mlbm.run_until(w, params, dt, za, zb, [5, -1, 5, 5])
+    assert e.value.code == mlbm.EINVAL
+    with pytest.raises(ValueError):
+        mlbm.run_until(w, params, dt, za, zb, [5, 5])
 
 
 def test_weights_objects_with_smaller_halos_leave_earlier_ones_usable():
