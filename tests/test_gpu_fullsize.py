@@ -90,3 +90,42 @@ def test_full_size_fp32_tracks_fp64(big):
         del a, b, res
     s = mlbm.norms(w, out[mlbm.F32][1], out[mlbm.F64][1], out[mlbm.F32][2], out[mlbm.F64][2])
     assert np.sqrt(s[0] / s[1]) < 1e-6
+
+
+def test_largest_cloud_one_step_sampled_parity():
+    """Four times the benchmark's node count: 4096^2 jittered nodes (16.8 M), N_L = 12, P_2,
+    FP32 tile layout only, stencils built on the device.  Sampled stencils equal the oracle's
+    brute force over all nodes, and one FP32 step matches the oracle's step at those nodes."""
+    n_side, k, deg = 4096, 12, 2
+    xy = mi.jittered_lattice(n_side, 0.3, seed=5)
+    dx = 1.0 / n_side
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=k, degree=deg, dx_ml=dx),
+                             device=True)
+    w = mlbm.build_weights(cloud, keep=mlbm.KEEP_W32)
+    assert w.n_bad == 0 and w.n == n_side * n_side
+    n = w.n
+    rho, u, v = mi.tgv_initial(xy, U0)
+    perm = cloud.perm()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(n)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:0")
+    params = [(TAU, 0.0, 1.0)]
+    f0 = torch.empty(9 * n, dtype=torch.float32, device="cuda:0")
+    f1 = torch.empty_like(f0)
+    mom = torch.empty(3 * n, dtype=torch.float32, device="cuda:0")
+    mlbm.init(w, params, mlbm.F32, t(rho), t(u), t(v), f0)
+    mlbm.step(w, params, mlbm.F32, f0, f1, mom)
+    got = mom.view(3, n).cpu().numpy().astype(np.float64)
+    del f0, f1, mom
+    st_gpu = cloud.stencil(0)
+    rng = np.random.default_rng(23)
+    for i in rng.choice(n, 8, replace=False):
+        sidx, W = oracle.node_weights(xy, int(i), k, deg, dx, box=(1.0, 1.0))
+        np.testing.assert_array_equal(st_gpu[:, i], sidx[1])
+        members = np.unique(sidx)
+        pos = {m: q for q, m in enumerate(members)}
+        post = oracle.collide_field(oracle.init_equilibrium(rho[members], u[members], v[members]), TAU)
+        f1n = np.array([sum(W[kk, j] * post[kk, pos[sidx[kk, j]]] for j in range(k)) for kk in range(9)])
+        r_o, u_o, v_o = oracle.moments(f1n)
+        m = got[:, inv[i]]
+        assert abs(m[0] - r_o) < 1e-7 and abs(m[1] - u_o) < 1e-8 and abs(m[2] - v_o) < 1e-8, (i, m, r_o, u_o, v_o)
