@@ -523,6 +523,57 @@ def bench_shan_chen(n_side: int = 2048, steps: int = 200, warmup: int = 5):
             "dtype": "f32", "G": sc[0]}
 
 
+def bench_tgv_4096(steps: int = 50, warmup: int = 5):
+    """The large Taylor-Green recipe at four times the benchmark's node count: 4096^2 jittered
+    nodes (16.8 M), N_L 30, P_4, dx_ml = h, FP32 tile layout only (about 50 GB on the device with
+    the FP64 shape vectors); FP32 steps timed with CUDA events, inputs far larger than L2."""
+    import torch
+
+    import mlbm_inputs as mi
+    import paper_2306_01525_gb300 as mlbm
+
+    n_side, K, deg, tau, u0 = 4096, 30, 4, 0.8, 0.01
+    xy = mi.jittered_lattice(n_side, 0.3, seed=7)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=1.0 / n_side),
+                             device=True)
+    torch.cuda.synchronize()
+    t_cloud = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w = mlbm.build_weights(cloud, keep=mlbm.KEEP_W32)
+    torch.cuda.synchronize()
+    t_weights = time.perf_counter() - t0
+    del cloud
+    n = w.n
+    params = [(tau, 0.0, 1.0)]
+    rho, u, v = (torch.as_tensor(a, dtype=torch.float64, device=dev) for a in mi.tgv_initial(xy, u0))
+    a = torch.empty(9 * n, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F32, rho, u, v, a)
+    del rho, u, v
+    a = mlbm.run(w, params, mlbm.F32, a, b, warmup)
+    b = b if a is not b else torch.empty_like(a)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    mlbm.run(w, params, mlbm.F32, a, b, steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = _peaks()
+    gbs = step_bytes_per_node(K, 4) * n / (ms * 1e-3) / 1e9
+    out = {"workload": "tgv_4096sq_k30_d4", "nodes": n, "steps": steps, "dtype": "f32",
+           "value": n / (ms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms,
+           "algorithmic_bytes_per_node": step_bytes_per_node(K, 4), "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
+           "setup_s": {"cloud_device": t_cloud, "weights_gpu": t_weights},
+           "device_memory_in_use_gb": (lambda fm: (fm[1] - fm[0]) / 1e9)(torch.cuda.mem_get_info())}
+    del a, b, w
+    return out
+
+
 def bench_tgv_small(steps: int = 500, reps: int = 20):
     """The paper's Taylor-Green case as configured for plain MLBM in FP64: 32 x 32 jittered
     lattice (1024 nodes), N_L 12, P_2, tau 0.8, u0 0.01, dx_ml = h, 500 steps; a cloud this small
@@ -868,6 +919,8 @@ def run_mlbm(args):
         torch.cuda.empty_cache()
         extras["tgv_small"] = bench_tgv_small()
         torch.cuda.empty_cache()
+        extras["tgv_4096"] = bench_tgv_4096()
+        torch.cuda.empty_cache()
         extras["shan_chen"] = bench_shan_chen()
         torch.cuda.empty_cache()
         extras["paper_sweep"] = bench_paper_sweep("f64")
@@ -918,7 +971,8 @@ def main():
                     help="stencil rule of the main workload (own-node or nearest-node)")
     ap.add_argument("--ratio", type=float, default=1.0, help="dx_ml / h of the main workload")
     ap.add_argument("--leg", default=None,
-                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep", "tgv_small"],
+                    choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep", "tgv_small",
+                             "tgv_4096"],
                     help="run only this extra measurement and print it")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --leg: the leg's step count (annulus: its step cap), e.g. for a short ncu capture")
@@ -937,6 +991,7 @@ def main():
         legs = {"batched": lambda: bench_batched(n or 1000),
                 "annulus": lambda: bench_annulus(n or 500000, min(2000, n or 2000)),
                 "tgv_small": lambda: bench_tgv_small(n or 500),
+                "tgv_4096": lambda: bench_tgv_4096(n or 50),
                 "adjoint": lambda: bench_adjoint(n or 2000), "lattice_lbm": bench_lattice,
                 "shan_chen": bench_shan_chen,
                 "paper_sweep": lambda: bench_paper_sweep("f64")}
