@@ -864,7 +864,7 @@ def run_mlbm(args):
     # Through the C ABI with host buffers (mlbm_step_host): every step copies its input state
     # from pinned host memory, steps it and copies the result back; the batch's steps are
     # independent, so the library overlaps the copies of neighbouring steps with the compute.
-    e2e_steps = max(4, min(20, args.steps))
+    e2e_steps = max(4, min(50, args.steps))
     st_bytes = 9 * N * 4
     h_in = torch.empty(9 * N, dtype=torch.float32, pin_memory=True)
     h_out = [torch.empty(9 * N, dtype=torch.float32, pin_memory=True) for _ in range(2)]
