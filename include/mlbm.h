@@ -391,7 +391,11 @@ int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const 
  * shape vectors; without it, or when |1 - 1/tau| < 1/16 in any segment (fhat is not
  * recoverable near tau = 1), fhat is recomputed from s_prev.  Both routes agree to rounding.
  * lam_next and lam_prev: device [9][N] dtype; lam_prev must alias neither lam_next nor s_next.
- * Segments must use MLBM_STENCIL_OWN (else MLBM_EINVAL).
+ * Both stencil rules: under MLBM_STENCIL_NEAREST the transposed interpolation runs over the
+ * nodes whose departure-node stencils hold each node.  A weights object with any
+ * MLBM_STENCIL_NEAREST segment needs s_next and |1 - 1/tau| >= 1/16 in every segment (else
+ * MLBM_EINVAL, nothing launched).  The first call builds the transposed tables (host work and
+ * a device copy of the departure nodes, then kept with the weights).
  * ------------------------------------------------------------------------------------- */
 int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtype,
                       const void *s_prev, const void *s_next, const void *lam_next,

@@ -404,18 +404,23 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
 }
 
 // Coefficients of the sliced entry table: thread (t, b) fills the entries of the tile's b-th
-// row (slice b / 32, lane b % 32): entry e of that row is csr entry csr_ptr[m] + e, q = j n + i
-// (member j of node i, segment-local), with coefficients c_kj(i), k = 1..8, in the step's
-// precision (the FP32 values round the FP64 shape vectors as the forward's FP32 layout does, and
-// the FP32 centre coefficient adds them up in member order as the forward's interpolation
-// does); entries past the row's end (padding) get zeros.
+// row m (slice b / 32, lane b % 32).  The entry at position q reads node i = src[q]: its
+// coefficient for direction k is the weight with which f_k(m) enters fhat_k(i), i.e. c_kj(i)
+// for the member j of the stencil that interpolates (i, k) (the stencil of the departure node
+// L_k(i), or of i itself under the own-node rule) with s_j = m, and 0 if m is not a member.
+// jh[q] >= 0 gives j directly (own-node rows, from the transposed stencil); else it is looked
+// up.  c_kj(i) = W_k[j](i) in the step's precision (the FP32 values round the FP64 shape vectors
+// as the forward's FP32 layout does), except the FP32 difference form's centre, 1 - sum_{j>=1}
+// W_k[j](i) added up in member order as the forward does.  Padding (src -1) gets zeros.
 template <typename T>
 __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, int B, const SegDev *__restrict__ seg,
                                 const uint16_t *__restrict__ rowp, const int64_t *__restrict__ sbeg,
-                                const int32_t *__restrict__ slen, const int32_t *__restrict__ csr_ptr,
-                                const int32_t *__restrict__ csr_ent, const double *__restrict__ w64c,
+                                const int32_t *__restrict__ slen, const int32_t *__restrict__ srcs,
+                                const int8_t *__restrict__ jhs, const int32_t *__restrict__ idx,
+                                const int32_t *__restrict__ near, const double *__restrict__ w64c,
                                 T *__restrict__ coef) {
     constexpr bool kDev = std::is_same<T, float>::value;
+    constexpr int W = V<T>::width, NV = 8 / W;
     const int64_t total = (int64_t)ntiles * B;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int t = (int)(g / B), b = (int)(g - (int64_t)t * B);
@@ -423,21 +428,26 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
         const int ws = t * (B / 32) + (b >> 5);
         const int L = slen[ws];
         if (L == 0) continue;
-        const bool row = b < tile.count;
         const SegDev sd = seg[tile.seg];
-        const int64_t m = tile.begin + (row ? rowp[g] : 0);
-        const int32_t e0 = row ? csr_ptr[m] : 0, e1 = row ? csr_ptr[m + 1] : 0;
+        const int64_t m = tile.begin + (b < tile.count ? rowp[g] : 0);
         for (int e = 0; e < L; ++e) {
             const int64_t qb = sbeg[ws] + (int64_t)32 * e;  // first entry of the slice's row e
+            const int64_t q = qb + (b & 31);
             T v[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = T(0);
-            if (e0 + e < e1) {
-                const int64_t ent = csr_ent[e0 + e];
-                const int64_t j = ent / sd.n, i = ent - j * sd.n;
+            const int32_t src = b < tile.count ? srcs[q] : -1;
+            if (src >= 0) {
+                const int64_t i = src - sd.off;
                 const double *wk = w64c + sd.w_off + i;
-#pragma unroll
                 for (int k = 0; k < 8; ++k) {
+                    int j = jhs[q];
+                    if (j < 0) {  // member of the departure node's stencil equal to m, if any
+                        const int64_t Lk = near ? near[8 * sd.off + (int64_t)k * sd.n + i] - sd.off : i;
+                        for (int jj = 0; jj < sd.K && j < 0; ++jj)
+                            if (idx[sd.idx_off + (int64_t)jj * sd.n + Lk] == m) j = jj;
+                    }
+                    if (j < 0) continue;
                     if (j > 0 || !kDev) {
                         v[k] = (T)wk[((int64_t)k * sd.K + j) * sd.n];
                     } else {
@@ -448,7 +458,6 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
                 }
             }
             // planes: vector h (directions h W .. h W + W - 1) of lane b % 32 at (qb NV + 32 h + lane) W
-            constexpr int W = V<T>::width, NV = 8 / W;
 #pragma unroll
             for (int k = 0; k < 8; ++k) coef[(qb * NV + 32 * (k / W) + (b & 31)) * W + k % W] = v[k];
         }
@@ -613,31 +622,79 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
             (rc = cuda_check_step(cudaMemcpy(ent.data(), w->d_csr_ent, sizeof(int32_t) * ent.size(),
                                              cudaMemcpyDeviceToHost), "transposed stencil")))
             return rc;
+        // nearest-node segments: which nodes depart to each node, per direction (inverse of the
+        // departure map), [seg] -> per direction k: offsets [n + 1] and readers
+        std::vector<int32_t> near;
+        std::vector<std::vector<std::vector<int32_t>>> inv_ptr(w->nseg), inv_ent(w->nseg);
+        if (w->any_nearest) {
+            near.resize((size_t)8 * w->N);
+            if ((rc = cuda_check_step(cudaMemcpy(near.data(), w->d_near, sizeof(int32_t) * near.size(),
+                                                 cudaMemcpyDeviceToHost), "departure nodes")))
+                return rc;
+            for (int sg = 0; sg < w->nseg; ++sg) {
+                const SegmentHost &h = w->seg[sg];
+                if (h.d.stencil_mode != MLBM_STENCIL_NEAREST) continue;
+                inv_ptr[sg].assign(8, {});
+                inv_ent[sg].assign(8, {});
+                for (int k = 0; k < 8; ++k) {
+                    const int32_t *nk = &near[(size_t)8 * h.off + (size_t)k * h.n];
+                    std::vector<int32_t> &pt = inv_ptr[sg][k], &en = inv_ent[sg][k];
+                    pt.assign((size_t)h.n + 1, 0);
+                    for (int64_t i = 0; i < h.n; ++i) pt[nk[i] - h.off + 1]++;
+                    for (int64_t L = 0; L < h.n; ++L) pt[L + 1] += pt[L];
+                    en.resize((size_t)h.n);
+                    std::vector<int32_t> fill(pt.begin(), pt.end() - 1);
+                    for (int64_t i = 0; i < h.n; ++i) en[fill[nk[i] - h.off]++] = (int32_t)(h.off + i);
+                }
+            }
+        }
         std::vector<uint16_t> rowp((size_t)nt * B, 0);
         std::vector<int32_t> slen((size_t)nt * WPT, 0);
         std::vector<std::vector<int32_t>> rh(nt);
         std::vector<std::vector<uint16_t>> sl(nt);
+        std::vector<std::vector<int32_t>> ps(nt);  // per tile, per position: reading node (-1 padding)
+        std::vector<std::vector<int8_t>> pj(nt);   // per tile, per position: member index hint
         std::vector<int> bad(nt, 0);
         auto work = [&](int t0, int t1) {
             std::vector<int32_t> others;
             std::vector<int> ord;
+            std::vector<std::vector<int32_t>> rs;  // per row of the tile: reading nodes
+            std::vector<std::vector<int8_t>> rj;   // and member index hints
             for (int t = t0; t < t1; ++t) {
                 const TileDev &T_ = tiles[t];
                 const SegmentHost &h = w->seg[T_.seg];
-                auto src_of = [&](int64_t q) { return (int32_t)(h.off + ent[q] % h.n); };
+                const bool nearest = h.d.stencil_mode == MLBM_STENCIL_NEAREST;
                 const int64_t m0 = T_.begin;
+                rs.assign(T_.count, {});
+                rj.assign(T_.count, {});
+                for (int b = 0; b < T_.count; ++b) {
+                    const int64_t m = m0 + b;
+                    std::vector<int32_t> &R = rs[b];
+                    if (!nearest) {  // the transposed stencil's entries (i, j), j-major: centre first
+                        for (int32_t q = ptr[m]; q < ptr[m + 1]; ++q) {
+                            R.push_back((int32_t)(h.off + ent[q] % h.n));
+                            rj[b].push_back((int8_t)(ent[q] / h.n));
+                        }
+                    } else {  // nodes whose departure node for some direction has m in its stencil
+                        for (int32_t q = ptr[m]; q < ptr[m + 1]; ++q) {
+                            const int64_t L = ent[q] % h.n;
+                            for (int k = 0; k < 8; ++k)
+                                for (int32_t r = inv_ptr[T_.seg][k][L]; r < inv_ptr[T_.seg][k][L + 1]; ++r)
+                                    R.push_back(inv_ent[T_.seg][k][r]);
+                        }
+                        std::sort(R.begin(), R.end());
+                        R.erase(std::unique(R.begin(), R.end()), R.end());
+                        rj[b].assign(R.size(), (int8_t)-1);
+                    }
+                }
                 ord.resize(T_.count);
                 for (int b = 0; b < T_.count; ++b) ord[b] = b;
-                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
-                    return ptr[m0 + x + 1] - ptr[m0 + x] > ptr[m0 + y + 1] - ptr[m0 + y];
-                });
+                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return rs[x].size() > rs[y].size(); });
                 others.clear();
                 for (int b = 0; b < T_.count; ++b) {
                     rowp[(size_t)t * B + b] = (uint16_t)ord[b];
-                    for (int32_t q = ptr[m0 + b]; q < ptr[m0 + b + 1]; ++q) {
-                        const int32_t s = src_of(q);
-                        if (s < m0 || s >= m0 + T_.count) others.push_back(s);
-                    }
+                    for (int32_t s_ : rs[b])
+                        if (s_ < m0 || s_ >= m0 + T_.count) others.push_back(s_);
                 }
                 std::sort(others.begin(), others.end());
                 others.erase(std::unique(others.begin(), others.end()), others.end());
@@ -645,33 +702,36 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                     bad[t] = 1;
                     continue;
                 }
-                std::vector<int32_t> &R = rh[t];
-                R.resize((size_t)T_.count + others.size());
-                for (int b = 0; b < T_.count; ++b) R[b] = (int32_t)(m0 + b);
-                std::copy(others.begin(), others.end(), R.begin() + T_.count);
-                auto slot_of = [&](int32_t s) -> uint16_t {
-                    if (s >= m0 && s < m0 + T_.count) return (uint16_t)(s - m0);
-                    return (uint16_t)(T_.count + (std::lower_bound(others.begin(), others.end(), s) - others.begin()));
+                std::vector<int32_t> &RH = rh[t];
+                RH.resize((size_t)T_.count + others.size());
+                for (int b = 0; b < T_.count; ++b) RH[b] = (int32_t)(m0 + b);
+                std::copy(others.begin(), others.end(), RH.begin() + T_.count);
+                auto slot_of = [&](int32_t s_) -> uint16_t {
+                    if (s_ >= m0 && s_ < m0 + T_.count) return (uint16_t)(s_ - m0);
+                    return (uint16_t)(T_.count + (std::lower_bound(others.begin(), others.end(), s_) - others.begin()));
                 };
                 int64_t n_ent = 0;
                 for (int ws = 0; ws < WPT; ++ws) {
                     int L = 0;
-                    for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
-                        const int r = ord[32 * ws + l];
-                        L = std::max(L, (int)(ptr[m0 + r + 1] - ptr[m0 + r]));
-                    }
+                    for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) L = std::max(L, (int)rs[ord[32 * ws + l]].size());
                     slen[(size_t)t * WPT + ws] = L;
                     n_ent += 32 * (int64_t)L;
                 }
                 std::vector<uint16_t> &S = sl[t];
                 S.assign((size_t)n_ent, 0);
+                ps[t].assign((size_t)n_ent, -1);
+                pj[t].assign((size_t)n_ent, (int8_t)-1);
                 int64_t base = 0;
                 for (int ws = 0; ws < WPT; ++ws) {
                     const int L = slen[(size_t)t * WPT + ws];
                     for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
                         const int r = ord[32 * ws + l];
-                        for (int32_t q = ptr[m0 + r]; q < ptr[m0 + r + 1]; ++q)
-                            S[base + 32 * (q - ptr[m0 + r]) + l] = slot_of(src_of(q));
+                        for (size_t e = 0; e < rs[r].size(); ++e) {
+                            const int64_t q = base + 32 * (int64_t)e + l;
+                            S[q] = slot_of(rs[r][e]);
+                            ps[t][q] = rs[r][e];
+                            pj[t][q] = rj[r][e];
+                        }
                     }
                     base += 32 * (int64_t)L;
                 }
@@ -687,8 +747,9 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
         for (int t = 0; t < nt; ++t)
             if (bad[t]) return fail(MLBM_EINVAL, "a tile's reverse halo exceeds 65535 nodes (stencils too spread out)");
         std::vector<int64_t> roff((size_t)nt), sbeg((size_t)nt * WPT);
-        std::vector<int32_t> rcnt((size_t)nt), rall;
+        std::vector<int32_t> rcnt((size_t)nt), rall, srcs;
         std::vector<uint16_t> slots;
+        std::vector<int8_t> jhs;
         int rmax = 0;
         for (int t = 0; t < nt; ++t) {
             roff[t] = (int64_t)rall.size();
@@ -701,8 +762,12 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                 base += 32 * (int64_t)slen[(size_t)t * WPT + ws];
             }
             slots.insert(slots.end(), sl[t].begin(), sl[t].end());
+            srcs.insert(srcs.end(), ps[t].begin(), ps[t].end());
+            jhs.insert(jhs.end(), pj[t].begin(), pj[t].end());
             std::vector<int32_t>().swap(rh[t]);
             std::vector<uint16_t>().swap(sl[t]);
+            std::vector<int32_t>().swap(ps[t]);
+            std::vector<int8_t>().swap(pj[t]);
         }
         w->adj_positions = (int64_t)slots.size();
         w->adj_rmax = rmax;
@@ -712,7 +777,9 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
             (rc = upload_vec(&w->d_adj_rcnt, rcnt, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_sbeg, sbeg, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_slen, slen, "adjoint tables")) ||
-            (rc = upload_vec(&w->d_adj_slot, slots, "adjoint tables")))
+            (rc = upload_vec(&w->d_adj_slot, slots, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_src, srcs, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_jh, jhs, "adjoint tables")))
             return rc;
     }
     const int i = std::is_same<T, float>::value ? 0 : 1;
@@ -724,7 +791,8 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nt * B + 255) / 256, 65536));
     adj_coef_kernel<T><<<grid, 256, 0, st>>>(w->d_tiles, nt, B, w->d_seg, w->d_adj_rowp, w->d_adj_sbeg, w->d_adj_slen,
-                                             w->d_csr_ptr, w->d_csr_ent, w->d_w64, (T *)w->d_adj_coef[i]);
+                                             w->d_adj_src, w->d_adj_jh, w->d_idx, w->d_near, w->d_w64,
+                                             (T *)w->d_adj_coef[i]);
     return cuda_check_step(cudaGetLastError(), "adjoint table launch");
 }
 
@@ -815,8 +883,6 @@ int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtyp
     if (s_next == lam_prev) return fail(MLBM_EINVAL, "s_next and lam_prev must not alias");
     int rc = check_dtype(w, dtype);
     if (rc) return rc;
-    if (w->any_nearest)
-        return fail(MLBM_EINVAL, "the adjoint step supports own-stencil segments only (MLBM_STENCIL_OWN)");
     mlbm_weights *wm = const_cast<mlbm_weights *>(w);
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = set_params(wm, params, st))) return rc;
@@ -824,6 +890,9 @@ int mlbm_adjoint_step(const mlbm_weights *w, const mlbm_params *params, int dtyp
     // fhat from s_next only where 1 - 1/tau keeps it recoverable (see the top of this file)
     for (int s = 0; s < w->nseg && s_next; ++s)
         if (!(std::fabs(1.0 - 1.0 / params[s].tau) >= 1.0 / 16)) s_next = nullptr;
+    if (!s_next && w->any_nearest)
+        return fail(MLBM_EINVAL, "the adjoint of nearest-node stencils needs the forward's next state (s_next) and "
+                                 "|1 - 1/tau| >= 1/16 in every segment");
     return dtype == MLBM_F32 ? adjoint_step_t<float>(wm, s_prev, s_next, lam_next, lam_prev, grad, st)
                              : adjoint_step_t<double>(wm, s_prev, s_next, lam_next, lam_prev, grad, st);
 }

@@ -194,6 +194,9 @@ struct mlbm_weights_impl {
     int64_t *d_adj_sbeg = nullptr;
     int32_t *d_adj_slen = nullptr;
     uint16_t *d_adj_slot = nullptr;
+    int32_t *d_adj_src = nullptr;  // per entry: reading node (stored position; -1 padding)
+    int8_t *d_adj_jh = nullptr;    // per entry: row node's member index in the reader's stencil, -1: find it
+    int32_t *d_near = nullptr;     // nearest-node clouds: per segment [8][n] departure nodes (stored positions)
     void *d_adj_coef[2] = {nullptr, nullptr};
     int64_t adj_positions = 0;
     int adj_rmax = 0;  // largest reverse halo

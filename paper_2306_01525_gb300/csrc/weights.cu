@@ -416,6 +416,9 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_adj_sbeg);
     cudaFree(w->d_adj_slen);
     cudaFree(w->d_adj_slot);
+    cudaFree(w->d_adj_src);
+    cudaFree(w->d_adj_jh);
+    cudaFree(w->d_near);
     for (void *b : w->d_adj_coef) cudaFree(b);
     for (void *b : w->d_stage) cudaFree(b);
     for (void *q : w->copy_stream)
@@ -747,6 +750,8 @@ int mlbm_build_weights(const mlbm_cloud *c, int flags, void *stream, mlbm_weight
         rc = upload(&w->d_sys_node, sn.data(), sn.size(), "system table");
         if (!rc) rc = upload(&w->d_sys_q, sq.data(), sq.size(), "system table");
         if (!rc) rc = upload(&w->d_sys_tgt, stg.data(), stg.size(), "system table");
+        // departure nodes, kept for the adjoint's transposed interpolation
+        if (!rc) rc = upload(&w->d_near, c->near.data(), c->near.size(), "departure nodes");
     }
     if (!rc) rc = solve_weights(w, d_x, d_y, st, 0, &nbad);
     cudaFree(w->d_sys_node);

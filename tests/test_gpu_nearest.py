@@ -145,10 +145,100 @@ def test_fixed_streaming_distance_converges_to_lattice_lbm_error():
     assert e4[0] < e2[0] and e4[1] < e2[1], (e2, e4)
 
 
-def test_adjoint_refuses_nearest_mode():
-    xy, cloud, w = _periodic_nearest(12, 9, 2, 2.0 / 12, seed=9)
-    f = torch.zeros(9 * w.n, dtype=torch.float64, device=DEV)
+def _rand_state(w, params, n, seed, dtype=mlbm.F64):
+    rng = np.random.default_rng(seed)
+    td = torch.float64 if dtype == mlbm.F64 else torch.float32
+    f = torch.empty(9 * w.n, dtype=td, device=DEV)
+    mlbm.init(w, params, dtype, _t(1 + 1e-3 * rng.standard_normal(n)), _t(3e-3 * rng.standard_normal(n)),
+              _t(3e-3 * rng.standard_normal(n)), f)
+    f += _t(1e-4 * rng.standard_normal(9 * w.n)).to(td)  # off-equilibrium part
+    return f
+
+
+def _step(w, params, s, dtype=mlbm.F64):
+    out = torch.empty_like(s)
+    mlbm.step(w, params, dtype, s, out)
+    return out
+
+
+def _nearest_cloud(kind, device=False):
+    if kind == "annulus":
+        xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[1000], seed=3)
+        seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=15, degree=2, dx_ml=1.0 / 20,
+                   stencil_mode=mlbm.STENCIL_NEAREST)
+    else:
+        n_side = int(kind)
+        xy = mi.jittered_lattice(n_side, 0.3, seed=n_side)
+        seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=16 if n_side < 100 else 12,
+                   degree=3 if n_side < 100 else 2, dx_ml=2.0 / n_side, stencil_mode=mlbm.STENCIL_NEAREST)
+    return xy, mlbm.build_weights(mlbm.build_cloud(xy, seg, device=device))
+
+
+@pytest.mark.parametrize("kind", ["24", "annulus", "200", "600"])
+def test_adjoint_nearest_matches_finite_differences(kind):
+    """The reverse step of a nearest-node cloud (each population interpolated in its departure
+    node's stencil, Sec. 2.3) against central differences of the forward: the transposed step
+    <lam_prev, v> and dL/dtau, dL/dg.  Periodic clouds with dx_ml = 2 h (departure nodes other
+    than the node itself) at 576, 40 k and 360 k nodes (one-warp, 128- and 512-node tiles), and
+    an annulus with bounce-back walls."""
+    xy, w = _nearest_cloud(kind, device=kind in ("200", "600"))
+    tau, g = 0.8, 1e-5
+    params = [(tau, g, 1.0)]
+    s = _rand_state(w, params, xy.shape[1], seed=41)
+    rng = np.random.default_rng(42)
+    lam = _t(rng.standard_normal(9 * w.n))
+    v = _t(rng.standard_normal(9 * w.n))
+    lam_prev = torch.empty_like(lam)
     grad = torch.zeros(2, dtype=torch.float64, device=DEV)
-    with pytest.raises(mlbm.MLBMError) as e:
-        mlbm.adjoint_step(w, [(0.8, 0.0, 1.0)], mlbm.F64, f, f.clone(), f.clone(), grad)
-    assert e.value.code == mlbm.EINVAL
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad, s_next=_step(w, params, s))
+    eps = 1e-5
+    fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
+    assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
+    for c, h in ((0, 1e-6), (1, 1e-6)):
+        hi, lo = list(params[0]), list(params[0])
+        hi[c] += h
+        lo[c] -= h
+        f = (torch.dot(lam, _step(w, [tuple(hi)], s)) - torch.dot(lam, _step(w, [tuple(lo)], s))) / (2 * h)
+        assert float(grad[c]) == pytest.approx(float(f), rel=1e-6), c
+
+
+def test_adjoint_nearest_fp32_close_to_fp64_and_deterministic():
+    """FP32 reverse step of a nearest-node annulus (transpose of the forward's difference form to
+    the departure node's value) against the FP64 reverse step, and bit-for-bit repeatable."""
+    xy, w = _nearest_cloud("annulus")
+    params = [(0.9, 2e-5, 1.0)]
+    n = xy.shape[1]
+    rng = np.random.default_rng(43)
+    fields = [_t(1 + 1e-3 * rng.standard_normal(n)), _t(3e-3 * rng.standard_normal(n)),
+              _t(3e-3 * rng.standard_normal(n))]
+    pert = _t(1e-4 * rng.standard_normal(9 * w.n))
+    lam = _t(rng.standard_normal(9 * w.n))
+    out = {}
+    for dt, td in ((mlbm.F64, torch.float64), (mlbm.F32, torch.float32)):
+        s = torch.empty(9 * w.n, dtype=td, device=DEV)
+        mlbm.init(w, params, dt, *fields, s)
+        s += pert.to(td)
+        sn = _step(w, params, s, dt)
+        res = []
+        for _ in range(2):
+            lp = torch.empty(9 * w.n, dtype=td, device=DEV)
+            g = torch.zeros(2, dtype=torch.float64, device=DEV)
+            mlbm.adjoint_step(w, params, dt, s, lam.to(td), lp, g, s_next=sn)
+            res.append((lp, g))
+        assert torch.equal(res[0][0], res[1][0]) and torch.equal(res[0][1], res[1][1])
+        out[dt] = (res[0][0].double(), res[0][1])
+    a, b = out[mlbm.F64][0], out[mlbm.F32][0]
+    assert float(torch.linalg.norm(a - b) / torch.linalg.norm(a)) < 1e-5
+    np.testing.assert_allclose(out[mlbm.F32][1].cpu().numpy(), out[mlbm.F64][1].cpu().numpy(), rtol=1e-4)
+
+
+def test_adjoint_nearest_needs_next_state():
+    """Nearest-node clouds take the reverse step from the forward's output only: without s_next,
+    or with |1 - 1/tau| < 1/16 (where that route is ill-conditioned), the call is refused."""
+    xy, cloud, w = _periodic_nearest(12, 9, 2, 2.0 / 12, seed=9)
+    f = _rand_state(w, [(0.8, 0.0, 1.0)], xy.shape[1], seed=44)
+    grad = torch.zeros(2, dtype=torch.float64, device=DEV)
+    for tau, sn in ((0.8, None), (1.02, f.clone())):
+        with pytest.raises(mlbm.MLBMError) as e:
+            mlbm.adjoint_step(w, [(tau, 0.0, 1.0)], mlbm.F64, f, f.clone(), f.clone(), grad, s_next=sn)
+        assert e.value.code == mlbm.EINVAL
