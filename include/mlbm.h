@@ -283,12 +283,13 @@ int mlbm_step_host(mlbm_weights *w, const mlbm_params *params, int dtype, int64_
  *   2. psi_i = rho_psi (1 - exp(-rho_i / rho_psi)) of the density of fhat;
  *   3. F_i = -G psi_i sum_k omega_k psi(x_i + e_k dx_ml) e_k, psi at x_i + e_k dx_ml (the
  *      departure point of the opposite direction) interpolated with the streaming's own
- *      shape vectors;
+ *      shape vectors, in the stencil that interpolates that departure point (the node's own,
+ *      or under MLBM_STENCIL_NEAREST that of the point's nearest node);
  *   4. BGK collision of fhat towards f^eq(rho, u + tau F / rho), plus the body force term of
  *      mlbm_step.
  *
- *   w          weights of periodic segments with own stencils only (no walls, no
- *              MLBM_STENCIL_NEAREST): MLBM_EINVAL otherwise.
+ *   w          weights of periodic segments (no walls: MLBM_EINVAL otherwise; a wall would
+ *              need a value of psi beyond it, a wetting choice), either stencil rule.
  *   params     host, nseg parameter sets as mlbm_step (tau, body force g, rho0).
  *   sc         host, nseg pairs {G, rho_psi}: coupling (with rho_psi = 1, G < -4 separates
  *              phases) and the density scale of psi (> 0).

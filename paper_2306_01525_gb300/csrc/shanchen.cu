@@ -16,8 +16,11 @@
 //      points with the same tile-layout shape vectors, form F, collide fhat in place.
 // The velocity shift is applied as (s^eq(u + tau F / rho) - s^eq(u)) / tau on top of the plain
 // collision (the same thing written as a difference), so the FP32 path keeps its exact mass
-// and momentum projection.  Periodic own-stencil segments only (no walls, no nearest-node
-// stencils).
+// and momentum projection.  Both stencil rules: under the nearest-node rule (Sec. 2.3) psi at
+// the departure point of direction k is interpolated in that point's own stencil (that of its
+// nearest node), with the streaming's per-direction slots and shape vectors.  Periodic segments
+// only (no walls: the model needs a wall value of psi, a wetting choice, that the method leaves
+// open).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -63,8 +66,78 @@ __device__ __forceinline__ T sc_exp(T x) {
         return exp(x);
 }
 
+// Values at the departure points x_b - e_k dx_ml of node b, k = 1..8 (out[k - 1]), under the
+// nearest-node rule: direction k is interpolated in the stencil of its departure node, member 0
+// being that node, through the per-direction halo slots ([ceil(K/2)][B][8] packed pairs) and
+// the tile-layout shape vectors.  val(k, slot) reads direction k's value at a halo slot.
+// Members are taken in the order, and in the forms, of the step kernel's nearest-node
+// interpolation (FP32: differences to the departure node's value; FP64: the literal sum), so a
+// step without interaction gives the plain step's populations bit for bit.
+template <typename T, int B, typename Val>
+__device__ __forceinline__ void interp_departure(const uint32_t *__restrict__ lidx, const T *__restrict__ wt,
+                                                 const TileDev &tile, int b, Val val, T (&out)[8]) {
+    using VT = typename V<T>::type;
+    constexpr bool kLiteral = !std::is_same<T, float>::value;
+    constexpr int W = V<T>::width;
+    constexpr int NV = 8 / W;
+    const int K = tile.K, JP = (K + 1) / 2;
+    const uint4 *__restrict__ lp = reinterpret_cast<const uint4 *>(lidx + tile.l_off) + 2 * b;
+    const VT *__restrict__ wbase = reinterpret_cast<const VT *>(wt + (kLiteral ? tile.w64_off : tile.w_off)) + b;
+    auto slot_words = [&](int jp, uint32_t (&pr)[8]) {
+        const uint4 lo = __ldcs(lp + (int64_t)jp * 2 * B), hi = __ldcs(lp + (int64_t)jp * 2 * B + 1);
+        pr[0] = lo.x; pr[1] = lo.y; pr[2] = lo.z; pr[3] = lo.w;
+        pr[4] = hi.x; pr[5] = hi.y; pr[6] = hi.z; pr[7] = hi.w;
+    };
+    T acc[8], c[8];
+    {
+        uint32_t pr[8];
+        slot_words(0, pr);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            c[k] = val(k, (int)(pr[k] & 0xFFFFu));
+            acc[k] = T(0);
+        }
+    }
+    for (int jp = 0; jp < JP; ++jp) {
+        uint32_t pr[8];
+        slot_words(jp, pr);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = 2 * jp + h;
+            if (j >= K) break;
+            if (!kLiteral && j == 0) continue;
+            const VT *__restrict__ wr = wbase + (int64_t)(kLiteral ? j : j - 1) * NV * B;
+            T wk[8];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vunpack(wk + q * W, __ldcs(wr + (int64_t)q * B));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const T x = val(k, h ? (int)(pr[k] >> 16) : (int)(pr[k] & 0xFFFFu));
+                acc[k] = kLiteral ? fma(wk[k], x, acc[k]) : fma(wk[k], x - c[k], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) out[k] = kLiteral ? acc[k] : c[k] + acc[k];
+}
+
+// The streamed populations f (storage form) of node p into fout, psi(rho of f) into psi.
+template <typename T>
+__device__ __forceinline__ void sc_store_streamed(const ScArgs<T> &a, int seg, int64_t p, const T (&f)[9]) {
+    constexpr bool kLiteral = !std::is_same<T, float>::value;
+    const T *pr = a.params + 4 * seg;
+    const T rho_ref = kLiteral ? T(0) : pr[2];
+    const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+    const T rho = rho_ref + drho;
+    const T rp = a.sc[2 * seg + 1];
+    a.psi[p] = rp * (T(1) - sc_exp(-rho / rp));
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * a.N + p] = f[k];
+}
+
 // Pass 1: fhat of every node of the tile (storage form) into fout, psi(rho of fhat) into psi.
-template <typename T, int B>
+// kNear: some tiles use nearest-node stencils (their halo staged direction-major, [8][U]).
+template <typename T, int B, bool kNear>
 __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_stream_kernel(ScArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
@@ -75,10 +148,26 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_stre
     const int64_t N = a.N;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
-        stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
+        const bool near = kNear && tile.mode == MLBM_STENCIL_NEAREST;
+        if (near)
+            stage_halo_dirmajor<T>(a.halo + tile.h_off, tile.U, a.fin, N, reinterpret_cast<T *>(sh));
+        else
+            stage_halo<T>(a.halo + tile.h_off, tile.U, a.fin, N, sh);
         __syncthreads();
         const int b = threadIdx.x;
-        if (b < tile.count) {
+        if (b < tile.count && near) {
+            if constexpr (kNear) {
+                const int64_t p = tile.begin + b;
+                const T *shs = reinterpret_cast<const T *>(sh);
+                const int U = tile.U;
+                T f[9], fk[8];
+                f[0] = a.fin[p];
+                interp_departure<T, B>(a.lidx, a.wt, tile, b, [&](int k, int sl) { return shs[k * U + sl]; }, fk);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) f[k + 1] = fk[k];
+                sc_store_streamed<T>(a, tile.seg, p, f);
+            }
+        } else if (b < tile.count) {
             const int64_t p = tile.begin + b;
             T f[9];
             f[0] = a.fin[p];
@@ -106,14 +195,7 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_stre
                 else
                     vunpack_sum(f + 1 + q * W, c[q], acc[q]);
             }
-            const T *pr = a.params + 4 * tile.seg;
-            const T rho_ref = kLiteral ? T(0) : pr[2];
-            const T drho = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-            const T rho = rho_ref + drho;
-            const T rp = a.sc[2 * tile.seg + 1];
-            a.psi[p] = rp * (T(1) - sc_exp(-rho / rp));
-#pragma unroll
-            for (int k = 0; k < 9; ++k) a.fout[(int64_t)k * N + p] = f[k];
+            sc_store_streamed<T>(a, tile.seg, p, f);
         }
         __syncthreads();
     }
@@ -121,7 +203,7 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_stre
 
 // Pass 2: psi at the eight departure points of every node, the interaction force, and the
 // collision of fhat (read from and written back to fout) towards the shifted equilibrium.
-template <typename T, int B>
+template <typename T, int B, bool kNear>
 __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_collide_kernel(ScArgs<T> a) {
     using VT = typename V<T>::type;
     constexpr bool kLiteral = !std::is_same<T, float>::value;
@@ -140,43 +222,51 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_coll
             const T pc = shp[b];
             // psi_k = psi at x - e_k dx_ml, k = 1..8: FP32 as differences to the centre value,
             // FP64 as the literal sum (the forms of the streaming)
-            T acc[8];
-            const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
-            const VT *__restrict__ wp;
-            if constexpr (kLiteral) {
-                wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
-#pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    T w0[W];
-                    vunpack(w0, __ldcs(wp + (int64_t)q * B));
-#pragma unroll
-                    for (int r = 0; r < W; ++r) acc[q * W + r] = w0[r] * pc;
-                }
-                wp += (int64_t)NV * B;
+            T psik[8];
+            if (kNear && tile.mode == MLBM_STENCIL_NEAREST) {
+                if constexpr (kNear)
+                    interp_departure<T, B>(a.lidx, a.wt, tile, b, [&](int, int sl) { return shp[sl]; }, psik);
             } else {
-                wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
+                T acc[8];
+                const uint32_t *__restrict__ lp = a.lidx + tile.l_off + b;
+                const VT *__restrict__ wp;
+                if constexpr (kLiteral) {
+                    wp = reinterpret_cast<const VT *>(a.wt + tile.w64_off) + b;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) acc[k] = T(0);
-            }
-            const int m1 = tile.K - 1;
-            for (int j = 0; j < m1; ++j) {
-                const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
-                const int sl = (j & 1) ? (int)(pr >> 16) : (int)(pr & 0xFFFFu);
-                const T x = kLiteral ? shp[sl] : shp[sl] - pc;
+                    for (int q = 0; q < NV; ++q) {
+                        T w0[W];
+                        vunpack(w0, __ldcs(wp + (int64_t)q * B));
 #pragma unroll
-                for (int q = 0; q < NV; ++q) {
-                    T wv[W];
-                    vunpack(wv, __ldcs(wp + (int64_t)(j * NV + q) * B));
+                        for (int r = 0; r < W; ++r) acc[q * W + r] = w0[r] * pc;
+                    }
+                    wp += (int64_t)NV * B;
+                } else {
+                    wp = reinterpret_cast<const VT *>(a.wt + tile.w_off) + b;
 #pragma unroll
-                    for (int r = 0; r < W; ++r) acc[q * W + r] = fma(wv[r], x, acc[q * W + r]);
+                    for (int k = 0; k < 8; ++k) acc[k] = T(0);
                 }
+                const int m1 = tile.K - 1;
+                for (int j = 0; j < m1; ++j) {
+                    const uint32_t pr = __ldcs(lp + (int64_t)(j >> 1) * B);
+                    const int sl = (j & 1) ? (int)(pr >> 16) : (int)(pr & 0xFFFFu);
+                    const T x = kLiteral ? shp[sl] : shp[sl] - pc;
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        T wv[W];
+                        vunpack(wv, __ldcs(wp + (int64_t)(j * NV + q) * B));
+#pragma unroll
+                        for (int r = 0; r < W; ++r) acc[q * W + r] = fma(wv[r], x, acc[q * W + r]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) psik[k] = kLiteral ? acc[k] : pc + acc[k];
             }
             // F = -G psi sum_k omega_k psi(x + e_k dx) e_k = G psi sum_k omega_k e_k psi_k, since
             // x - e_k dx = x + e_k' dx with e_k' = -e_k
             T sx = T(0), sy = T(0);
 #pragma unroll
             for (int k = 1; k < 9; ++k) {
-                const T pk = kLiteral ? acc[k - 1] : pc + acc[k - 1];
+                const T pk = psik[k - 1];
                 sx += omega_of<T>(k) * T(ex_of(k)) * pk;
                 sy += omega_of<T>(k) * T(ey_of(k)) * pk;
             }
@@ -221,13 +311,13 @@ __global__ void __launch_bounds__(B, tile_min_blocks(B, (int)sizeof(T))) sc_coll
     }
 }
 
-template <typename T, int B>
+template <typename T, int B, bool kNear>
 int launch_sc_t(mlbm_weights *w, const ScArgs<T> &a, cudaStream_t st) {
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, w->device);
     const size_t sm1 = (size_t)w->umax * 8 * sizeof(T), sm2 = (size_t)w->umax * sizeof(T);
     if (sm1 > (size_t)maxsm) return fail(MLBM_EINVAL, "a tile's halo does not fit in shared memory at this precision");
-    const void *k1 = (const void *)sc_stream_kernel<T, B>, *k2 = (const void *)sc_collide_kernel<T, B>;
+    const void *k1 = (const void *)sc_stream_kernel<T, B, kNear>, *k2 = (const void *)sc_collide_kernel<T, B, kNear>;
     int rc = allow_dynamic_smem(k1);
     if (!rc) rc = allow_dynamic_smem(k2);
     if (rc) return rc;
@@ -236,8 +326,8 @@ int launch_sc_t(mlbm_weights *w, const ScArgs<T> &a, cudaStream_t st) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, B, sm2);
     const int g1 = std::max(1, std::min(w->ntiles, std::max(1, per1) * w->num_sms));
     const int g2 = std::max(1, std::min(w->ntiles, std::max(1, per2) * w->num_sms));
-    sc_stream_kernel<T, B><<<g1, B, sm1, st>>>(a);
-    sc_collide_kernel<T, B><<<g2, B, sm2, st>>>(a);
+    sc_stream_kernel<T, B, kNear><<<g1, B, sm1, st>>>(a);
+    sc_collide_kernel<T, B, kNear><<<g2, B, sm2, st>>>(a);
     return cuda_check_step(cudaGetLastError(), "Shan-Chen step launch");
 }
 
@@ -288,7 +378,10 @@ int sc_step_t(mlbm_weights *w, const void *fin, void *fout, void *mom, cudaStrea
     a.mom = (T *)mom;
     a.N = w->N;
     a.ntiles = w->ntiles;
-    return with_tile_nodes(w->tile_nodes, [&](auto Bc) { return launch_sc_t<T, decltype(Bc)::value>(w, a, st); });
+    return with_tile_nodes(w->tile_nodes, [&](auto Bc) {
+        return w->any_nearest ? launch_sc_t<T, decltype(Bc)::value, true>(w, a, st)
+                              : launch_sc_t<T, decltype(Bc)::value, false>(w, a, st);
+    });
 }
 
 }  // namespace
@@ -303,8 +396,8 @@ extern "C" int mlbm_sc_step(mlbm_weights *w, const mlbm_params *params, const ml
     if (f_in == f_out) return fail(MLBM_EINVAL, "f_in and f_out must not alias");
     int rc = check_dtype(w, dtype);
     if (rc) return rc;
-    if (w->has_mask || w->any_nearest)
-        return fail(MLBM_EINVAL, "Shan-Chen steps need periodic segments with own stencils (no walls, MLBM_STENCIL_OWN)");
+    if (w->has_mask)
+        return fail(MLBM_EINVAL, "Shan-Chen steps need periodic segments (no walls)");
     cudaStream_t st = (cudaStream_t)stream;
     if ((rc = set_params(w, params, st))) return rc;
     if ((rc = set_sc_params(w, sc, st))) return rc;

@@ -22,8 +22,9 @@ def _t(a):
     return torch.as_tensor(a, dtype=torch.float64, device=DEV)
 
 
-def _periodic(xy, K, deg, dx):
-    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx)
+def _periodic(xy, K, deg, dx, mode="own"):
+    seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=deg, dx_ml=dx,
+               stencil_mode=mlbm.STENCIL_NEAREST if mode == "paper" else mlbm.STENCIL_OWN)
     cloud = mlbm.build_cloud(xy, seg)
     return cloud, mlbm.build_weights(cloud)
 
@@ -48,11 +49,14 @@ def _from_stored(a, perm, dtype, rho0=1.0):
     return out
 
 
+@pytest.mark.parametrize("mode", ["own", "paper"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_no_interaction_is_the_plain_step(dtype):
+def test_no_interaction_is_the_plain_step(dtype, mode):
+    """G = 0: the Shan-Chen step is the plain step bit for bit, under both stencil rules (the
+    nearest-node rule with dx_ml = 2 h, departure points beyond the own stencil)."""
     dt = mlbm.F32 if dtype == "f32" else mlbm.F64
     xy = mi.jittered_lattice(32, 0.3, seed=31)
-    _, w = _periodic(xy, 16, 3, 0.5 / 32)
+    _, w = _periodic(xy, 16, 3, (2.0 if mode == "paper" else 0.5) / 32, mode)
     params = [(0.8, 0.0, 1.0)]
     rho, u, v = mi.tgv_initial(xy, 0.02)
     td = torch.float32 if dt == mlbm.F32 else torch.float64
@@ -65,16 +69,19 @@ def test_no_interaction_is_the_plain_step(dtype):
     assert torch.equal(b, c) and torch.equal(mb, mc)
 
 
+@pytest.mark.parametrize("mode", ["own", "paper"])
 @pytest.mark.parametrize("n_side,K,deg,steps", [(24, 16, 3, 20), (200, 12, 2, 4)])
-def test_fp64_steps_match_the_oracle_step_by_step(n_side, K, deg, steps):
+def test_fp64_steps_match_the_oracle_step_by_step(n_side, K, deg, steps, mode):
     """Oracle shape vectors uploaded; the state after every step is the oracle's Shan-Chen
     post-collision state to 1e-12 relative, and the moments are those of the streamed state.
-    24^2 nodes run one-warp tiles, 200^2 the 128-node tiles."""
+    24^2 nodes run one-warp tiles, 200^2 the 128-node tiles.  Under the nearest-node rule
+    (dx_ml = 2 h) psi at each departure point is interpolated in its nearest node's stencil, as
+    the oracle's paper mode does."""
     tau, G = 1.0, -5.0
-    dx = 0.5 / n_side
+    dx = (2.0 if mode == "paper" else 0.5) / n_side
     xy = mi.jittered_lattice(n_side, 0.3, seed=32)
-    cloud, w = _periodic(xy, K, deg, dx)
-    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0))
+    cloud, w = _periodic(xy, K, deg, dx, mode)
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode=mode)
     w.upload(W[1:], oracle.stencils(xy, K, box=(1.0, 1.0)).astype(np.int32))
     n = xy.shape[1]
     rng = np.random.default_rng(5)
@@ -97,12 +104,13 @@ def test_fp64_steps_match_the_oracle_step_by_step(n_side, K, deg, steps):
         np.testing.assert_allclose(m[0][np.argsort(perm)], r, rtol=1e-12)
 
 
-def test_fp32_follows_the_fp64_oracle():
+@pytest.mark.parametrize("mode", ["own", "paper"])
+def test_fp32_follows_the_fp64_oracle(mode):
     n_side, K, deg, tau, G = 24, 16, 3, 1.0, -5.0
-    dx = 0.5 / n_side
+    dx = (2.0 if mode == "paper" else 0.5) / n_side
     xy = mi.jittered_lattice(n_side, 0.3, seed=33)
-    cloud, w = _periodic(xy, K, deg, dx)
-    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0))
+    cloud, w = _periodic(xy, K, deg, dx, mode)
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode=mode)
     w.upload(W[1:], oracle.stencils(xy, K, box=(1.0, 1.0)).astype(np.int32))
     n = xy.shape[1]
     rng = np.random.default_rng(6)
@@ -209,7 +217,9 @@ def test_flat_interfaces_reach_the_coexistence_densities(dtype):
     assert abs(r.sum() - rho.sum()) <= 2e-2 * rho.sum()
 
 
-def test_walls_and_nearest_node_stencils_are_refused():
+def test_walls_are_refused():
+    """Walls would need a value of psi beyond the wall (a wetting choice the method leaves
+    open): a cloud with bounce-back nodes is refused."""
     xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[1000], seed=3)
     c = mlbm.build_cloud(xy, dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=12, degree=2, dx_ml=0.05))
     w = mlbm.build_weights(c)
@@ -217,11 +227,47 @@ def test_walls_and_nearest_node_stencils_are_refused():
     with pytest.raises(mlbm.MLBMError) as e:
         mlbm.sc_step(w, [(0.8, 0.0, 1.0)], (-5.0, 1.0), mlbm.F64, a, a.clone())
     assert e.value.code == mlbm.EINVAL
-    xy = mi.jittered_lattice(16, 0.3, seed=2)
-    c = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=9, degree=2, dx_ml=2.0 / 16,
-                                  stencil_mode=mlbm.STENCIL_NEAREST))
-    w = mlbm.build_weights(c)
-    a = torch.zeros(9 * w.n, dtype=torch.float64, device=DEV)
-    with pytest.raises(mlbm.MLBMError) as e:
-        mlbm.sc_step(w, [(0.8, 0.0, 1.0)], (-5.0, 1.0), mlbm.F64, a, a.clone())
-    assert e.value.code == mlbm.EINVAL
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_mixed_stencil_rules_batched_equal_single_runs(dtype):
+    """An own-rule and a nearest-rule segment in one weights object (one launch per pass over
+    both): each segment's Shan-Chen steps equal its own single-segment run.  The nearest
+    segment bit for bit; the own segment to rounding, because a build holding any nearest
+    segment solves every segment through the departure-point table, whose offsets
+    (x_i - e_k dx_ml) - x_i round differently from -e_k dx_ml (FP64 shape vectors equal to
+    about 1e-16)."""
+    dt = mlbm.F32 if dtype == "f32" else mlbm.F64
+    td = torch.float32 if dt == mlbm.F32 else torch.float64
+    parts = [mi.jittered_lattice(20, 0.3, seed=61), mi.jittered_lattice(16, 0.3, seed=62)]
+    segs = [dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=12, degree=2, dx_ml=0.5 / 20),
+            dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=16, degree=3, dx_ml=2.0 / 16,
+                 stencil_mode=mlbm.STENCIL_NEAREST)]
+    params = [(1.0, 0.0, 1.0), (0.9, 0.0, 1.0)]
+    scp = [(-5.0, 1.0), (-4.5, 1.0)]
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    wb = mlbm.build_weights(mlbm.build_cloud(xy, segs, offs))
+    rng = np.random.default_rng(63)
+    rho = LN2 * (1 + 0.05 * rng.standard_normal(xy.shape[1]))
+    zero = np.zeros(xy.shape[1])
+
+    def run(w, prm, sc, r, n):
+        a = torch.empty(9 * w.n, dtype=td, device=DEV)
+        mlbm.init(w, prm, dt, _t(r), _t(zero[:n]), _t(zero[:n]), a)
+        b = torch.empty_like(a)
+        for _ in range(5):
+            mlbm.sc_step(w, prm, sc, dt, a, b)
+            a, b = b, a
+        return a.view(9, -1)
+
+    got = run(wb, params, scp, rho, xy.shape[1])
+    for s in range(2):
+        ws = mlbm.build_weights(mlbm.build_cloud(parts[s], segs[s]))
+        ref = run(ws, [params[s]], [scp[s]], rho[offs[s]:offs[s + 1]], parts[s].shape[1])
+        g = got[:, offs[s]:offs[s + 1]]
+        if s == 1:
+            assert torch.equal(g, ref)
+        else:
+            tol = 1e-13 if dt == mlbm.F64 else 1e-6
+            assert float((g - ref).abs().max()) <= tol * float(ref.abs().max())
