@@ -369,19 +369,22 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
             VT acc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) vzero(acc[q]);
-            // four entries per pass: their slots and coefficients are loaded before any is used
+            // kE entries per pass: their slots and coefficients are loaded before any is used.
+            // Eight when the cotangents come from s_next, four when they are read from the
+            // node-major buffer (the widths that measured fastest on each route)
+            constexpr int kE = kFromNext ? 8 : 4;
             int e = 0;
-            for (; e + 3 < L; e += 4) {
-                int sl[4];
-                VT c[4][NV];
+            for (; e + kE - 1 < L; e += kE) {
+                int sl[kE];
+                VT c[kE][NV];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
+                for (int r = 0; r < kE; ++r) {
                     sl[r] = sp[(int64_t)32 * (e + r)];
 #pragma unroll
                     for (int q = 0; q < NV; ++q) c[r][q] = __ldcs(cp + ((int64_t)32 * (e + r)) * NV + 32 * q);
                 }
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < kE; ++r)
 #pragma unroll
                     for (int q = 0; q < NV; ++q) vfma_acc(acc[q], c[r][q], sh[sl[r] * NV + q]);
             }
