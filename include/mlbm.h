@@ -196,7 +196,9 @@ int mlbm_weights_download(const mlbm_weights *w, int seg, double *W);
 /* Replace the shape vectors of segment seg with caller-supplied FP64 values (same layout as
  * mlbm_weights_download); both the FP64 and the FP32 copies held are overwritten.  idx
  * (host, [N_L][n_seg] int32, layout of mlbm_cloud_stencil) must equal the library's own
- * stencil, else MLBM_EINVAL and nothing changes.  Synchronous. */
+ * stencil, else MLBM_EINVAL and nothing changes.  Synchronous; the adjoint's coefficients,
+ * if built, are discarded (after a device synchronisation) and rebuilt from the new shape
+ * vectors on the next mlbm_adjoint_step. */
 int mlbm_weights_upload(mlbm_weights *w, int seg, const double *W, const int32_t *idx);
 
 /* ---------------------------------------------------------------------------------------

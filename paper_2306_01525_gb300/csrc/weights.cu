@@ -829,6 +829,15 @@ int mlbm_weights_upload(mlbm_weights *w, int seg, const double *W, const int32_t
                          "upload weights")))
         return rc;
     if ((rc = repack_weights(w, nullptr))) return rc;
+    // the adjoint's transposed coefficients hold the old shape vectors: drop them, so the next
+    // reverse step rebuilds them (its slot tables depend on the stencils only, checked above)
+    if (w->d_adj_coef[0] || w->d_adj_coef[1]) {
+        if ((rc = cuda_check(cudaDeviceSynchronize(), "upload weights"))) return rc;
+        for (void *&c : w->d_adj_coef) {
+            cudaFree(c);
+            c = nullptr;
+        }
+    }
     return MLBM_OK;
 }
 

@@ -358,3 +358,31 @@ def test_adjoint_step_batched_segments_match_finite_differences(taus):
             f = (torch.dot(lam, _step(w, [tuple(p) for p in hi], s)) -
                  torch.dot(lam, _step(w, [tuple(p) for p in lo], s))) / (2 * h)
             assert float(grad[2 * seg + c]) == pytest.approx(float(f), rel=1e-6), (seg, c)
+
+
+def test_upload_after_adjoint_rebuilds_its_coefficients():
+    """Shape vectors uploaded after a reverse step replace the adjoint's transposed
+    coefficients too: the next reverse step equals that of a fresh weights object holding the
+    uploaded vectors, bit for bit (and differs from the step before the upload)."""
+    xy, dx, cloud, w, _, _ = _annulus(upload=False)
+    params = [(0.9, 2e-5, 1.0)]
+    s = _rand_state(w, params, xy, seed=21)
+    rng = np.random.default_rng(22)
+    lam = _t(rng.standard_normal(9 * w.n))
+
+    def reverse(wt):
+        lp = torch.empty_like(lam)
+        g = torch.zeros(2, dtype=torch.float64, device=DEV)
+        mlbm.adjoint_step(wt, params, mlbm.F64, s, lam, lp, g, s_next=_step(wt, params, s))
+        return lp, g
+
+    before, _ = reverse(w)
+    sidx, W = oracle.weights(xy, 15, 2, dx)
+    idx = sidx[1].astype(np.int32)
+    w.upload(W[1:], idx)
+    after, g_after = reverse(w)
+    fresh = mlbm.build_weights(cloud)
+    fresh.upload(W[1:], idx)
+    ref, g_ref = reverse(fresh)
+    assert torch.equal(after, ref) and torch.equal(g_after, g_ref)
+    assert not torch.equal(after, before)

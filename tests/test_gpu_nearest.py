@@ -280,3 +280,46 @@ def test_rollout_gradient_nearest_matches_central_differences():
     assert gtau == pytest.approx(fdt, rel=1e-5)
     assert gg == pytest.approx(fdg, rel=1e-5)
     assert gr == pytest.approx(fdr, rel=1e-6)
+
+
+def test_rollout_gradient_nearest_matches_oracle_autograd():
+    """Nearest-node annulus with walls, the oracle's paper-mode shape vectors uploaded: the
+    gradients of a 40-step FP64 rollout (tau, g and the initial fields) equal those of the
+    oracle's autograd reference, whose streaming gathers each direction through its own
+    (departure-node) stencil."""
+    from oracle import torch_ref
+    from paper_2306_01525_gb300.autograd import rollout
+
+    xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[1000], seed=3)
+    K, deg, dx = 15, 2, 1.0 / 20
+    seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=K, degree=deg, dx_ml=dx,
+               stencil_mode=mlbm.STENCIL_NEAREST)
+    cloud = mlbm.build_cloud(xy, seg)
+    w = mlbm.build_weights(cloud)
+    sidx, W = oracle.weights(xy, K, deg, dx, mode="paper")
+    w.upload(W[1:], oracle.stencils(xy, K).astype(np.int32))
+    n = xy.shape[1]
+    tau, g, steps = 0.9, 5e-5, 40
+    rng = np.random.default_rng(46)
+    rho0 = 1 + 1e-4 * rng.standard_normal(n)
+    u0, v0 = 1e-4 * rng.standard_normal(n), 1e-4 * rng.standard_normal(n)
+    tgt = 1e-3 * rng.standard_normal(n)
+
+    def loss(r, u, v, T):
+        return torch.sum((u - T(tgt)) ** 2 + v ** 2) + torch.sum((r - 1.0) ** 2)
+
+    G = lambda a: torch.tensor(a, dtype=torch.float64, device=DEV, requires_grad=True)
+    tt, gt, r0, a0, b0 = G(tau), G(g), G(rho0), G(u0), G(v0)
+    r, u, v = rollout(w, tt, gt, r0, a0, b0, steps, dtype=mlbm.F64)
+    loss(r, u, v, lambda a: torch.as_tensor(a, dtype=torch.float64, device=DEV)).backward()
+    C = lambda a: torch.tensor(a, dtype=torch.float64, requires_grad=True)
+    tc, gc, rc0, ac0, bc0 = C(tau), C(g), C(rho0), C(u0), C(v0)
+    mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
+    fdir = oracle.azimuthal_force(xy, 1.0)
+    rr, uu, vv = torch_ref.rollout(sidx, W, tc, gc, fdir, mask, rc0, ac0, bc0, steps)
+    loss(rr, uu, vv, lambda a: torch.as_tensor(a, dtype=torch.float64)).backward()
+    assert tt.grad.item() == pytest.approx(tc.grad.item(), rel=1e-8)
+    assert gt.grad.item() == pytest.approx(gc.grad.item(), rel=1e-8)
+    for gpu, ref in ((r0, rc0), (a0, ac0), (b0, bc0)):
+        np.testing.assert_allclose(gpu.grad.cpu().numpy(), ref.grad.numpy(), rtol=1e-7,
+                                   atol=1e-8 * np.abs(ref.grad.numpy()).max())
