@@ -448,6 +448,19 @@ def bench_adjoint(steps: int = 2000):
     rev_us = kernel_us(lambda: mlbm.adjoint_step(w, params, mlbm.F32, s, lam, lp, gacc, s_next=sn))
     rev_rc_us = kernel_us(lambda: mlbm.adjoint_step(w, params, mlbm.F32, s, lam, lp, gacc))
     fwd_us = kernel_us(lambda: mlbm.step(w, params, mlbm.F32, s, sn))
+    # the same cloud under the nearest-node rule (each direction interpolated in the stencil of
+    # its departure node): forward step and reverse step from s_next, timed the same way; the
+    # first reverse step (not timed) builds the transposed tables
+    wn = mlbm.build_weights(mlbm.build_cloud(
+        xy, dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=24, degree=3, dx_ml=dx,
+                 stencil_mode=mlbm.STENCIL_NEAREST), device=True))
+    s_n = torch.empty(9 * n, dtype=torch.float32, device=dev)
+    mlbm.init(wn, params, mlbm.F32, r0.detach(), a0.detach(), b0.detach(), s_n)
+    sn_n = torch.empty_like(s_n)
+    mlbm.step(wn, params, mlbm.F32, s_n, sn_n)
+    rev_near_us = kernel_us(lambda: mlbm.adjoint_step(wn, params, mlbm.F32, s_n, lam, lp, gacc, s_next=sn_n))
+    fwd_near_us = kernel_us(lambda: mlbm.step(wn, params, mlbm.F32, s_n, sn_n))
+    del wn
     K = 24
     bpn = adjoint_bytes_per_node(K)
     peak, _ = _peaks()
@@ -461,6 +474,7 @@ def bench_adjoint(steps: int = 2000):
             "reverse_step": {"us": rev_us, "us_recompute_route": rev_rc_us, "forward_step_us": fwd_us,
                              "algorithmic_bytes_per_node": bpn, "achieved_gbs": gbs,
                              "frac_of_hbm": gbs / peak,
+                             "nearest_rule": {"us": rev_near_us, "forward_step_us": fwd_near_us},
                              "l2": "flushed before each launch (256 MB write, then 256 MB read)"}}
 
 
