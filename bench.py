@@ -339,8 +339,9 @@ def bench_annulus(max_steps: int = 500000, chunk: int = 2000):
     a = torch.empty(9 * n, dtype=torch.float64, device=dev)
     b = torch.empty_like(a)
     mlbm.init(w, params, mlbm.F64, td(np.ones(n)), td(np.zeros(n)), td(np.zeros(n)), a)
-    # first use of every kernel of the loop below (on a fresh box the driver compiles torch's
-    # own kernels for this GPU on first use, outside the timed region here)
+    # first use of every kernel of the loop below (on a machine with an empty kernel cache the
+    # CUDA driver compiles torch's own kernels for this GPU on first use, outside the timed
+    # region here)
     _, u, v = mlbm.moments(w, params, mlbm.F64, a)
     mlbm.norms(w, u, u.clone(), v, v.clone())
     prev, done, res = None, 0, float("inf")
@@ -395,8 +396,9 @@ def bench_adjoint(steps: int = 2000):
     a0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
     b0 = torch.zeros(n, dtype=torch.float64, device=dev, requires_grad=True)
     # warm-up: a short rollout and its backward pass with the same loss (first use of the
-    # library's kernels, of autograd and of every torch kernel the loss launches: on a fresh box
-    # the driver compiles torch's kernels for this GPU on first use, seconds of host time)
+    # library's kernels, of autograd and of every torch kernel the loss launches: with an empty
+    # kernel cache the CUDA driver compiles torch's kernels for this GPU on first use, seconds
+    # of host time)
     rw, uw, vw = rollout(w, tt, gt, r0, a0, b0, 10, dtype=mlbm.F32)
     ((torch.sqrt(uw * uw + vw * vw + 1e-30) - target) ** 2).sum().backward()
     for p_ in (tt, gt, r0, a0, b0):
