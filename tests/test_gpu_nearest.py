@@ -323,3 +323,35 @@ def test_rollout_gradient_nearest_matches_oracle_autograd():
     for gpu, ref in ((r0, rc0), (a0, ac0), (b0, bc0)):
         np.testing.assert_allclose(gpu.grad.cpu().numpy(), ref.grad.numpy(), rtol=1e-7,
                                    atol=1e-8 * np.abs(ref.grad.numpy()).max())
+
+
+def test_adjoint_mixed_stencil_rules_matches_finite_differences():
+    """An own-rule and a nearest-rule segment in one weights object (one reverse step over both
+    kinds of transposed rows): <lam_prev, v> and each segment's dL/dtau, dL/dg against central
+    differences of the forward."""
+    parts = [mi.jittered_lattice(18, 0.3, seed=71), mi.jittered_lattice(16, 0.3, seed=72)]
+    segs = [dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=12, degree=2, dx_ml=0.7 / 18),
+            dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=16, degree=3, dx_ml=2.0 / 16,
+                 stencil_mode=mlbm.STENCIL_NEAREST)]
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    w = mlbm.build_weights(mlbm.build_cloud(xy, segs, offs))
+    params = [(0.8, 2e-5, 1.0), (0.7, -1e-5, 1.0)]
+    s = _rand_state(w, params, xy.shape[1], seed=73)
+    rng = np.random.default_rng(74)
+    lam = _t(rng.standard_normal(9 * w.n))
+    v = _t(rng.standard_normal(9 * w.n))
+    lam_prev = torch.empty_like(lam)
+    grad = torch.zeros(4, dtype=torch.float64, device=DEV)
+    mlbm.adjoint_step(w, params, mlbm.F64, s, lam, lam_prev, grad, s_next=_step(w, params, s))
+    eps = 1e-5
+    fd = (torch.dot(lam, _step(w, params, s + eps * v)) - torch.dot(lam, _step(w, params, s - eps * v))) / (2 * eps)
+    assert float(torch.dot(lam_prev, v)) == pytest.approx(float(fd), rel=1e-7)
+    for seg in range(2):
+        for c, h in ((0, 1e-6), (1, 1e-6)):
+            lo, hi = [list(p) for p in params], [list(p) for p in params]
+            lo[seg][c] -= h
+            hi[seg][c] += h
+            f = (torch.dot(lam, _step(w, [tuple(p) for p in hi], s)) -
+                 torch.dot(lam, _step(w, [tuple(p) for p in lo], s))) / (2 * h)
+            assert float(grad[2 * seg + c]) == pytest.approx(float(f), rel=1e-6), (seg, c)
