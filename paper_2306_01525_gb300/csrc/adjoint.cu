@@ -3,22 +3,26 @@
 // respect to tau, the body force g and the initial fields.
 //
 // Forward step (storage form s, lattice units): fhat = B (S s), s' = C(fhat; tau, g) with
-//   S  the interpolation fhat_k(i) = sum_j W_k[j](i) s_k(s_j(i))       (Sec. 2.3), in the form
-//      the forward kernel evaluates it: FP64 literally, FP32 as s_k(i) + sum_{j>=1} W (s_k(s_j) -
-//      s_k(i)), i.e. with centre coefficient 1 - sum_{j>=1} W_k[j](i)
+//   S  the interpolation fhat_k(i) = sum_j W_k[j](i) s_k(s_j(L))        (Sec. 2.3), L = i under
+//      the own-node rule and L = L_k(i), the node nearest to the departure point, under the
+//      nearest-node rule; in the form the forward kernel evaluates it: FP64 literally, FP32 as
+//      s_k(L) + sum_{j>=1} W (s_k(s_j) - s_k(L)), i.e. with centre coefficient
+//      1 - sum_{j>=1} W_k[j](i)
 //   B  the wall bounce-back fhat_k = fhat_k' on unknown populations      (Sec. 3)
 //   C  the BGK collision with forcing                                    (eq. LBM_collision, Sec. 3)
 // Reverse: mu = J_C^T lam, mut = B^T mu, lam_prev = S^T mut.  S^T is done as a pull over the
 // transposed stencil (for node m, the pairs (i, j) with s_j(i) = m, the centre pair (m, 0)
-// included), in a fixed order, so the result is deterministic without atomics.  Parameter
-// gradients are reduced per tile and then per segment in a fixed order.
+// included; under the nearest-node rule, every node i whose departure-node stencil holds m
+// for some direction, with a coefficient per direction), in a fixed order, so the result is
+// deterministic without atomics.  Parameter gradients are reduced per tile and then per
+// segment in a fixed order.
 //
 // J_C and dL/dtau need the moments and the non-equilibrium part of fhat.  When the caller
 // passes the forward's output s' = C(fhat) they come from it: the collision keeps rho and adds
 // exactly g to rho u, and s' - F - s^eq = (1 - 1/tau)(fhat - s^eq), so no shape vector is read.
 // Near tau = 1 that division loses fhat (at tau = 1, s' = s^eq + F whatever fhat was), so with
 // |1 - 1/tau| < 1/16 in any segment, or without s', fhat is recomputed from s with the forward's
-// own tile interpolation.
+// own tile interpolation (own-node rule only; nearest-node clouds need s').
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,9 +45,6 @@ int cuda_check_step(cudaError_t e, const char *what);
 namespace {
 
 constexpr int kThreads = 256;
-// rows per CTA of the transposed pull: one row per thread, a CTA per 128 rows, so that the
-// hardware's block scheduling balances the rows' uneven lengths
-constexpr int kPullThreads = 128;
 
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh) {
     sh[threadIdx.x] = a;
