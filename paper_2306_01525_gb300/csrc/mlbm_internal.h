@@ -67,10 +67,17 @@ constexpr int kTileNodes = 512;
 constexpr int kTileNodesSmall = 128;
 constexpr int kTileNodesTiny = 32;
 
+// Functions evaluated both by host code and inside kernels' launch bounds.
+#ifdef __CUDACC__
+#define MLBM_HOST_DEVICE __host__ __device__
+#else
+#define MLBM_HOST_DEVICE
+#endif
+
 // CTAs per SM that the tile kernels' register budget is set for: two 512-node CTAs per SM in
 // FP32 (one in FP64), the same threads per SM for 128-node tiles, at most 16 one-warp CTAs.
-constexpr int tile_min_blocks(int B, int elem_bytes) {
-    return std::min((elem_bytes == 4 ? 2 : 1) * (kTileNodes / B), 16);
+MLBM_HOST_DEVICE constexpr int tile_min_blocks(int B, int elem_bytes) {
+    return (elem_bytes == 4 ? 2 : 1) * (kTileNodes / B) < 16 ? (elem_bytes == 4 ? 2 : 1) * (kTileNodes / B) : 16;
 }
 
 // Tile size for a cloud whose segments have the given node counts.

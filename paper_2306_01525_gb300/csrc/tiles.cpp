@@ -91,7 +91,6 @@ int build_tiles(const mlbm_cloud *c, int B, std::vector<TileDev> &tiles, std::ve
                     }
                 }
             } else {
-                const int JP = (T.K + 1) / 2;
                 for (int k = 1; k <= 8; ++k)
                     for (int j = 0; j < T.K; ++j) {
                         const int jp = j >> 1, hi = j & 1;
