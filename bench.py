@@ -439,6 +439,10 @@ def bench_adjoint(steps: int = 2000):
         for _ in range(reps):
             flush.zero_()
             torch.sum(clean, dim=0, out=sink)
+            # a short device-side delay (about 50 us at 2 GHz) before the start event, so that
+            # the host has issued the call's launches before the device reaches the event and
+            # the interval holds device time only, not the host's argument handling
+            torch.cuda._sleep(100_000)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
