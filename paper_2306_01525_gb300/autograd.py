@@ -7,7 +7,11 @@ respect to the relaxation time tau, the body-force magnitude g and the three ini
 through the library's adjoint kernels (mlbm_moments_adjoint, mlbm_adjoint_step,
 mlbm_init_adjoint).  Only every ``checkpoint``-th state (default ceil(sqrt(nsteps))) is kept
 during the forward pass; the backward pass recomputes each segment of states from its
-checkpoint and sweeps it in reverse.  One segment (nseg == 1) per weights object.
+checkpoint and sweeps it in reverse.  One segment (nseg == 1) per weights object, either
+stencil rule; each reverse step gets the forward's next state, and under the nearest-node rule
+it needs |1 - 1/tau| >= 1/16 (near tau = 1 the interpolated populations cannot be recovered
+from that state, and only the own-node rule can recompute them), else the backward pass raises
+MLBMError.
 """
 from __future__ import annotations
 
