@@ -1,5 +1,6 @@
 """Pins of the oracle's autograd reference (oracle.torch_ref): its forward equals the C oracle,
-and its gradients equal central finite differences of the C oracle."""
+and its gradients equal central finite differences of the C oracle, under both stencil rules
+(the nearest-node rule with its per-direction stencils, Sec. 2.3)."""
 import numpy as np
 import pytest
 
@@ -10,10 +11,12 @@ torch = pytest.importorskip("torch")
 from oracle import torch_ref  # noqa: E402
 
 
-def _annulus_case(steps=30):
+def _annulus_case(steps=30, mode="own"):
     xy, _ = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[1000], seed=3)
-    dx = 1.0 / 40
-    sidx, W = oracle.weights(xy, 15, 2, dx)
+    dx = 1.0 / 40 if mode == "own" else 1.0 / 20
+    sidx, W = oracle.weights(xy, 15, 2, dx, mode=mode)
+    if mode == "paper":  # departure points interpolated outside the node's own stencil
+        assert np.any(sidx[1:, 0, :] != np.arange(xy.shape[1])[None, :])
     mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
     fdir = oracle.azimuthal_force(xy, 1.0)
     n = xy.shape[1]
@@ -35,8 +38,9 @@ def _loss(r, u, v, target):
     return ((u - target[0]) ** 2 + (v - target[1]) ** 2).sum() + ((r - 1.0) ** 2).sum()
 
 
-def test_torch_forward_equals_c_oracle():
-    xy, sidx, W, mask, fdir, rho0, u0, v0, steps = _annulus_case()
+@pytest.mark.parametrize("mode", ["own", "paper"])
+def test_torch_forward_equals_c_oracle(mode):
+    xy, sidx, W, mask, fdir, rho0, u0, v0, steps = _annulus_case(mode=mode)
     tau, g = 0.9, 3e-5
     want = _c_rollout(sidx, W, tau, g, fdir, mask, rho0, u0, v0, steps)
     t = lambda a: torch.as_tensor(a, dtype=torch.float64)
@@ -45,8 +49,9 @@ def test_torch_forward_equals_c_oracle():
         np.testing.assert_allclose(a.numpy(), b, rtol=0, atol=1e-13)
 
 
-def test_torch_gradients_equal_c_oracle_finite_differences():
-    xy, sidx, W, mask, fdir, rho0, u0, v0, steps = _annulus_case(20)
+@pytest.mark.parametrize("mode", ["own", "paper"])
+def test_torch_gradients_equal_c_oracle_finite_differences(mode):
+    xy, sidx, W, mask, fdir, rho0, u0, v0, steps = _annulus_case(20, mode)
     tau, g = 0.9, 3e-5
     rng = np.random.default_rng(2)
     target = (1e-3 * rng.standard_normal(u0.size), 1e-3 * rng.standard_normal(u0.size))
