@@ -26,15 +26,16 @@ def test_psi_special_values():
         assert d0 == pytest.approx(1.0, rel=1e-9)  # psi ~ rho for small densities
 
 
-def _periodic_cloud(n_side=16, K=12, deg=3, dx=None, seed=3):
+def _periodic_cloud(n_side=16, K=12, deg=3, dx=None, seed=3, mode="own"):
     xy = mi.jittered_lattice(n_side, 0.3, seed=seed)
     dx = dx if dx is not None else 0.5 / n_side
-    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0))
+    sidx, W = oracle.weights(xy, K, deg, dx, box=(1.0, 1.0), mode=mode)
     return xy, dx, sidx, W
 
 
-def test_no_interaction_is_the_plain_step():
-    xy, dx, sidx, W = _periodic_cloud()
+@pytest.mark.parametrize("mode", ["own", "paper"])
+def test_no_interaction_is_the_plain_step(mode):
+    xy, dx, sidx, W = _periodic_cloud(dx=(2.0 if mode == "paper" else 0.5) / 16, mode=mode)
     rho, u, v = mi.tgv_initial(xy, 0.02)
     f = oracle.init_equilibrium(rho, u, v)
     a = oracle.Stepper(sidx, W, 0.8)
@@ -45,12 +46,17 @@ def test_no_interaction_is_the_plain_step():
     np.testing.assert_array_equal(fa, fb)
 
 
-def test_force_of_a_quadratic_field_is_the_exact_gradient():
+@pytest.mark.parametrize("mode,dx", [("own", 0.03), ("paper", 0.1)])
+def test_force_of_a_quadratic_field_is_the_exact_gradient(mode, dx):
     """psi quadratic in x: interpolation with degree >= 2 is exact at every departure point and
-    sum_k omega_k psi(x + e_k d) e_k = d grad psi / 3 exactly, so F = -G psi d grad(psi) / 3."""
+    sum_k omega_k psi(x + e_k d) e_k = d grad psi / 3 exactly, so F = -G psi d grad(psi) / 3.
+    Under either stencil rule (the nearest-node rule with dx_ml above the spacing, so that the
+    departure points are interpolated in other nodes' stencils)."""
     xy = mi.jittered_lattice(14, 0.3, seed=5)  # no periodic box: stencils extrapolate at edges
-    dx, G = 0.03, -4.7
-    sidx, W = oracle.weights(xy, 12, 2, dx)
+    G = -4.7
+    sidx, W = oracle.weights(xy, 12, 2, dx, mode=mode)
+    if mode == "paper":
+        assert np.any(sidx[1:, 0, :] != np.arange(xy.shape[1])[None, :])
     x, y = xy
     q = 0.3 + 0.1 * x - 0.05 * y + 0.08 * x * x + 0.04 * x * y - 0.06 * y * y
     gx, gy = 0.1 + 0.16 * x + 0.04 * y, -0.05 + 0.04 * x - 0.12 * y
