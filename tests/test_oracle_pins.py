@@ -165,6 +165,47 @@ def test_annulus_profile_solves_azimuthal_balance():
     assert oracle.annulus_velocity(1.5, g, nu, r1, r2) > 0
 
 
+def test_residual_hand_computed():
+    """Sec. 3 stop rule, read as ||u^n - u^(n-1)||_2 / ||u^n||_2 over both velocity
+    components of all nodes: a 3-node field worked by hand.  Differences (0,-1,0) in u and
+    (0,0,1) in v give a numerator of 2; the new field's squares sum to 1 + 4 + 1 = 6, so the
+    residual is sqrt(2/6).  A missing square root (1/3), the old field in the denominator
+    (sqrt(2/8)) or a single component (sqrt(1/5)) all miss it."""
+    u_new, v_new = np.array([1.0, 0.0, 2.0]), np.array([0.0, 1.0, 0.0])
+    u_old, v_old = np.array([1.0, 1.0, 2.0]), np.array([0.0, 1.0, -1.0])
+    assert oracle.residual(u_new, v_new, u_old, v_old) == pytest.approx(np.sqrt(1.0 / 3.0), rel=1e-15)
+    # identical fields: zero; the residual is symmetric in neither argument order
+    assert oracle.residual(u_new, v_new, u_new, v_new) == 0.0
+    assert oracle.residual(u_old, v_old, u_new, v_new) == pytest.approx(np.sqrt(2.0 / 8.0), rel=1e-15)
+
+
+def test_speed_rel_error_hand_computed():
+    """eq. (vmag_error): e_i = | |U_i| - |U_i,true| | / |U_i,true| with |U| = sqrt(u^2 + v^2).
+    Node 0: |U| = 5 against a true speed of 4 gives 1/4 (dividing by the computed speed would
+    give 1/5).  Node 1: |U| = 1 against 5 gives 4/5 (positive: the absolute value).  Node 2:
+    a rotated velocity of the right magnitude has no speed error.  Node 3: at rest against a
+    true speed of 2 gives exactly 1."""
+    u = np.array([3.0, 0.6, 0.0, 0.0])
+    v = np.array([4.0, 0.8, -2.0, 0.0])
+    ut = np.array([0.0, 3.0, 2.0, 2.0])
+    vt = np.array([4.0, 4.0, 0.0, 0.0])
+    e = oracle.speed_rel_error(u, v, ut, vt)
+    np.testing.assert_allclose(e, [0.25, 0.8, 0.0, 1.0], rtol=1e-15, atol=0)
+
+
+def test_azimuthal_force_points_counter_clockwise():
+    """Sec. 3 annulus forcing g = (0, g) in polar coordinates (r, phi): the force is g times the
+    unit vector of increasing phi, (-sin phi, cos phi).  At (r, 0) it points along +y, at
+    (0, r) along -x, at (-r, 0) along -y; its magnitude is g everywhere."""
+    g = 2.5e-6
+    xy = np.array([[0.7, 0.0, -0.8, 0.0, 0.6],
+                   [0.0, 0.9, 0.0, -0.5, 0.8]])
+    gx, gy = oracle.azimuthal_force(xy, g)
+    np.testing.assert_allclose(gx, [0.0, -g, 0.0, g, -0.8 * g], rtol=1e-15, atol=1e-22)
+    np.testing.assert_allclose(gy, [g, 0.0, -g, 0.0, 0.6 * g], rtol=1e-15, atol=1e-22)
+    np.testing.assert_allclose(np.hypot(gx, gy), g, rtol=1e-15)
+
+
 # ----------------------------------------------------------------------------- shape vectors
 
 def _random_stencil(rng, K, jitter=1.0):
@@ -536,5 +577,9 @@ def test_annulus_steady_profile_matches_analytic():
     want = oracle.annulus_velocity(r / dx_ml, g, nu, 0.5 / dx_ml, 1.0 / dx_ml)
     interior = (r > 0.5 + 1e-9) & (r < 1.0 - 1e-9)
     assert oracle.l2_norm(np.hypot(u, v)[interior], np.abs(want[interior])) < 0.06
+    # signed: the flow turns the way the force pushes (counter-clockwise for g > 0), as
+    # eq. (bch_solution) gives it; a flipped force direction reverses u_theta and fails here
+    assert np.all(want[interior] > 0)
+    assert oracle.l2_norm(ut[interior], want[interior]) < 0.06
     ur = xy[0] / r * u + xy[1] / r * v
     assert np.max(np.abs(ur)) < 0.05 * np.max(np.abs(want))
