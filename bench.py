@@ -205,6 +205,22 @@ def _config(workload, world, ratio=1.0, stencil="own"):
     }
 
 
+def _sample_config(workload, ratio=1.0, stencil="own"):
+    """Config of what the CPU oracle is timed on: the bounded sample cloud (same recipe, stencil
+    size and degree as the GPU workload, fewer nodes).  GNUPS is a per-node-update rate, so the
+    sample's rate compares with the full workload's; the label names the cloud actually run."""
+    c = CPU_SAMPLE
+    N = c["n_side"] * c["n_side"]
+    return {
+        "workload": f"tgv_{c['n_side']}sq_k{c['K']}_d{c['deg']}",
+        "nodes": N, "stencil": c["K"], "degree": c["deg"], "tau": c["tau"], "u0": c["u0"],
+        "dx_ml": "h" if ratio == 1.0 else f"{ratio}h", "stencil_rule": stencil,
+        "geometry": "periodic unit square, lattice jittered +-0.3h",
+        "parallelism": "single",
+        "sample_of": _config(workload, 1, ratio, stencil)["workload"],
+    }
+
+
 def annulus_profile(r, g, nu, r1, r2):
     """Analytic azimuthal speed of force-driven flow between two circles, eq. (bch_solution):
     u(r) = -G (r^2 - alpha r + beta / r), G = g / (3 nu), alpha = (r1^2 + r1 r2 + r2^2) / (r1 + r2),
@@ -773,7 +789,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / done * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args.workload, 1, args.ratio, args.stencil),
+        "config": _sample_config(args.workload, args.ratio, args.stencil),
         "cpu_baseline": res,
         "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},

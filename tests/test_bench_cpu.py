@@ -68,3 +68,23 @@ def test_annulus_profile_matches_the_oracle_closed_form():
 def test_lattice_viscosity_reading():
     assert bench.lattice_nu(0.8) == pytest.approx(0.1)
     assert bench.lattice_nu(0.8) == pytest.approx(oracle.lattice_viscosity(0.8))
+
+
+def test_reference_line_names_the_sample_it_times(capsys):
+    """The reference arm times the oracle on the bounded sample cloud, so its config names that
+    cloud (128^2 nodes of the same recipe) and records which workload it samples."""
+    import json
+    import types
+
+    cfg = bench._sample_config("tgv_large")
+    c = bench.CPU_SAMPLE
+    assert cfg["workload"] == f"tgv_{c['n_side']}sq_k{c['K']}_d{c['deg']}" == "tgv_128sq_k30_d4"
+    assert cfg["nodes"] == 128 * 128
+    assert cfg["sample_of"] == bench._config("tgv_large", 1)["workload"] == "tgv_2048sq_k30_d4"
+    args = types.SimpleNamespace(steps=1, warmup=0, gpus=1, workload="tgv_large", ratio=1.0,
+                                 stencil="own")
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"]["workload"] == "tgv_128sq_k30_d4" and line["config"]["nodes"] == 16384
+    assert line["value"] == line["cpu_baseline"]["value"] == line["e2e"]["value"] > 0
