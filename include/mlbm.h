@@ -18,6 +18,12 @@
  *    stream) is enqueued asynchronously on that stream; errors raised by kernels surface at
  *    the next call that synchronises.  Nothing here falls back to the CPU: without a usable
  *    CUDA device every GPU entry point fails with MLBM_ECUDA.
+ *  - A weights object keeps one device copy of the step parameters (and of the Shan-Chen
+ *    couplings), refreshed on the calling stream when they change.  All calls that use one
+ *    weights object must therefore be ordered with one another: issue them on one stream (or
+ *    order the streams with events).  Two calls with different parameters on two unordered
+ *    streams race: the earlier call's kernels may read the later call's parameters.  Calls on
+ *    one weights object must not run concurrently from several host threads either.
  *  - Node order: the library stores nodes in Morton (Z-curve) order within each segment;
  *    "stored order" below means that order, "original order" the caller's input order.
  *    mlbm_cloud_perm gives the mapping.
@@ -371,9 +377,12 @@ int mlbm_lattice_step(int64_t nx, int64_t ny, const mlbm_params *params, int dty
  *               block order, so equal to rounding, not bitwise)
  * The call is stream-ordered and asynchronous (it does not synchronise).  The first call on
  * each device looks up the scratch array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture on the device.  All calls
- * share the one array and it keeps the last call's partial sums: calls that overlap on the
- * GPU (different streams or host threads without ordering) race and give wrong results.
+ * device current; make that first call before any stream capture on the device.  The
+ * address is kept for the life of the process: after a cudaDeviceReset (which recreates the
+ * device's context and reloads the library's device code) it is stale, so do not use this
+ * entry point across a device reset.  All calls share the one array and it keeps the last
+ * call's partial sums: calls that overlap on the GPU (different streams or host threads
+ * without ordering) race and give wrong results.
  * Errors: MLBM_EINVAL, MLBM_ECUDA.
  * ------------------------------------------------------------------------------------- */
 int mlbm_norms_noalloc(const double *a, const double *b, const double *c, const double *d,

@@ -57,3 +57,36 @@ def test_noalloc_norms_empty_and_limit():
     # beyond the limit: rejected on the host, nothing launched
     assert _call(a, a, None, None, LIMIT + 1, out) == mlbm.EINVAL
     assert b"limit" in mlbm.lib().mlbm_last_error()
+
+
+def test_noalloc_norms_leave_device_memory_untouched():
+    """The point of the entry point: after a first call (which looks up the scratch address),
+    further calls change the device's free memory by nothing.  The Python wrapper goes through
+    the same entry point and gives the same sums as the allocating one."""
+    w = _weights()
+    dev = torch.device("cuda:0")
+    n = 3_000_001
+    g = torch.Generator(device=dev).manual_seed(7)
+    a, b, c, d = (torch.randn(n, dtype=torch.float64, device=dev, generator=g) for _ in range(4))
+    out = torch.empty(3, dtype=torch.float64, device=dev)
+    assert _call(a, b, c, d, n, out) == mlbm.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        assert _call(a, b, c, d, n, out) == mlbm.OK
+        mlbm.norms_noalloc(a, b, c, d, out=out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0
+    np.testing.assert_allclose(out.cpu().numpy(), mlbm.norms(w, a, b, c, d), rtol=1e-13)
+
+
+def test_noalloc_norms_reject_one_sided_second_component():
+    """c and d come together or not at all: one of them alone is rejected before any launch."""
+    dev = torch.device("cuda:0")
+    a = torch.ones(16, dtype=torch.float64, device=dev)
+    out = torch.full((3,), float("nan"), dtype=torch.float64, device=dev)
+    assert _call(a, a, a, None, 16, out) == mlbm.EINVAL
+    assert _call(a, a, None, a, 16, out) == mlbm.EINVAL
+    assert b"both" in mlbm.lib().mlbm_last_error()
+    assert np.isnan(out.cpu().numpy()).all()
