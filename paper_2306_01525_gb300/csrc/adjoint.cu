@@ -413,16 +413,17 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
 // for the member j of the stencil that interpolates (i, k) (the stencil of the departure node
 // L_k(i), or of i itself under the own-node rule) with s_j = m, and 0 if m is not a member.
 // jh[q] >= 0 gives j directly (own-node rows, from the transposed stencil); else it is looked
-// up.  c_kj(i) = W_k[j](i) in the step's precision (the FP32 values round the FP64 shape vectors
-// as the forward's FP32 layout does), except the FP32 difference form's centre, 1 - sum_{j>=1}
-// W_k[j](i) added up in member order as the forward does.  Padding (src -1) gets zeros.
+// up.  c_kj(i) = W_k[j](i) in the step's precision (FP32: the rounded canonical FP32 shape
+// vectors the forward's FP32 layout is made of), except the FP32 difference form's centre,
+// 1 - sum_{j>=1} W_k[j](i) added up in member order as the forward does.  Padding (src -1) gets
+// zeros.
 template <typename T>
 __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, int B, const SegDev *__restrict__ seg,
                                 const uint16_t *__restrict__ rowp, const int64_t *__restrict__ sbeg,
                                 const int32_t *__restrict__ slen, const int32_t *__restrict__ srcs,
                                 const int8_t *__restrict__ jhs, const int32_t *__restrict__ idx,
                                 const int32_t *__restrict__ near, const double *__restrict__ w64c,
-                                T *__restrict__ coef) {
+                                const float *__restrict__ w32c, T *__restrict__ coef) {
     constexpr bool kDev = std::is_same<T, float>::value;
     constexpr int W = V<T>::width, NV = 8 / W;
     const int64_t total = (int64_t)ntiles * B;
@@ -444,6 +445,7 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
             if (src >= 0) {
                 const int64_t i = src - sd.off;
                 const double *wk = w64c + sd.w_off + i;
+                const float *wk32 = w32c + sd.w_off + i;
                 for (int k = 0; k < 8; ++k) {
                     int j = jhs[q];
                     if (j < 0) {  // member of the departure node's stencil equal to m, if any
@@ -452,11 +454,13 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
                             if (idx[sd.idx_off + (int64_t)jj * sd.n + Lk] == m) j = jj;
                     }
                     if (j < 0) continue;
-                    if (j > 0 || !kDev) {
+                    if (!kDev) {
                         v[k] = (T)wk[((int64_t)k * sd.K + j) * sd.n];
+                    } else if (j > 0) {
+                        v[k] = (T)wk32[((int64_t)k * sd.K + j) * sd.n];
                     } else {
                         float wsum = 0.f;
-                        for (int jj = 1; jj < sd.K; ++jj) wsum += (float)wk[((int64_t)k * sd.K + jj) * sd.n];
+                        for (int jj = 1; jj < sd.K; ++jj) wsum += wk32[((int64_t)k * sd.K + jj) * sd.n];
                         v[k] = (T)(1.f - wsum);
                     }
                 }
@@ -788,6 +792,7 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
     }
     const int i = std::is_same<T, float>::value ? 0 : 1;
     if (w->d_adj_coef[i]) return MLBM_OK;
+    if (i == 0 && !w->d_w32c) return fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
     if (cudaMalloc(&w->d_adj_coef[i], sizeof(T) * 8 * (size_t)std::max<int64_t>(1, w->adj_positions)) != cudaSuccess) {
         cudaGetLastError();
         w->d_adj_coef[i] = nullptr;
@@ -796,7 +801,7 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nt * B + 255) / 256, 65536));
     adj_coef_kernel<T><<<grid, 256, 0, st>>>(w->d_tiles, nt, B, w->d_seg, w->d_adj_rowp, w->d_adj_sbeg, w->d_adj_slen,
                                              w->d_adj_src, w->d_adj_jh, w->d_idx, w->d_near, w->d_w64,
-                                             (T *)w->d_adj_coef[i]);
+                                             w->d_w32c, (T *)w->d_adj_coef[i]);
     return cuda_check_step(cudaGetLastError(), "adjoint table launch");
 }
 

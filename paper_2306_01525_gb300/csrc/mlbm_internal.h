@@ -151,6 +151,9 @@ struct mlbm_weights_impl {
     int tile_nodes = 0;
     int32_t *d_idx = nullptr;
     double *d_w64 = nullptr;    // canonical FP64 shape vectors, per segment [8][K][n]
+    float *d_w32c = nullptr;    // canonical FP32 shape vectors, per segment [8][K][n], rounded so that
+                                // the polynomial reproduction holds as closely as FP32 allows
+    double *d_x = nullptr, *d_y = nullptr;  // node coordinates, stored order (for that rounding)
     float *d_w32t = nullptr;    // tile layout, FP32: [j-1][2][kTileNodes][4 directions], j = 1..K-1
     double *d_w64t = nullptr;   // tile layout, FP64: [j][4][kTileNodes][2 directions], j = 0..K-1
     uint32_t *d_lidx = nullptr; // packed 16-bit halo slots of stencil members 1..K-1

@@ -198,6 +198,52 @@ def test_fp32_rollout_gradient_close_to_fp64_reference():
     assert grads[mlbm.F32][1] == pytest.approx(grads[mlbm.F64][1], rel=1e-3)
 
 
+def test_fp32_rollout_gradient_within_1e4_of_oracle_and_finite_differences():
+    """The adjoint workload's recipe at test size: an annulus of about 2k scattered nodes,
+    N_L 24, P_3, tau 0.7, 300 FP32 steps with sqrt(T) checkpoints, loss = velocity-profile
+    mismatch against eq. (bch_solution).  The FP32 gradients with respect to tau, g and the
+    initial density agree with the oracle's autograd (FP64, same shape vectors) and with central
+    differences of the FP64 forward to 1e-4 relative."""
+    from paper_2306_01525_gb300.autograd import rollout
+
+    xy, dx, cloud, w, sidx, W = _annulus(h_key=2000, K=24, deg=3, dx=1.0 / 40, seed=5)
+    n = xy.shape[1]
+    tau, g, steps = 0.7, 1e-5, 300
+    rng = np.random.default_rng(21)
+    rho0 = 1 + 1e-4 * rng.standard_normal(n)
+    zeros = np.zeros(n)
+
+    def gpu(dtype, tau_, g_, grad):
+        tt = torch.tensor(tau_, dtype=torch.float64, device=DEV, requires_grad=grad)
+        gt = torch.tensor(g_, dtype=torch.float64, device=DEV, requires_grad=grad)
+        r0, a0, b0 = (torch.tensor(a, dtype=torch.float64, device=DEV, requires_grad=grad)
+                      for a in (rho0, zeros, zeros))
+        r, u, v = rollout(w, tt, gt, r0, a0, b0, steps, dtype=dtype)
+        L = _profile_loss(xy, r, u, v, g, tau, dx)
+        if not grad:
+            return float(L)
+        L.backward()
+        return tt.grad.item(), gt.grad.item(), r0.grad.cpu().numpy()
+
+    gtau, gg, grho = gpu(mlbm.F32, tau, g, True)
+    # oracle autograd reference
+    T = lambda a: torch.tensor(a, dtype=torch.float64, requires_grad=True)
+    tc, gc, rc0, ac0, bc0 = T(tau), T(g), T(rho0), T(zeros), T(zeros)
+    mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
+    fdir = oracle.azimuthal_force(xy, 1.0)
+    rr, uu, vv = torch_ref.rollout(sidx, W, tc, gc, fdir, mask, rc0, ac0, bc0, steps)
+    _profile_loss(xy, rr, uu, vv, g, tau, dx).backward()
+    assert gtau == pytest.approx(tc.grad.item(), rel=1e-4)
+    assert gg == pytest.approx(gc.grad.item(), rel=1e-4)
+    ref = rc0.grad.numpy()
+    assert np.linalg.norm(grho - ref) <= 1e-4 * np.linalg.norm(ref)
+    # central differences of the FP64 forward
+    fdt = (gpu(mlbm.F64, tau + 1e-5, g, False) - gpu(mlbm.F64, tau - 1e-5, g, False)) / 2e-5
+    fdg = (gpu(mlbm.F64, tau, g + 1e-8, False) - gpu(mlbm.F64, tau, g - 1e-8, False)) / 2e-8
+    assert gtau == pytest.approx(fdt, rel=1e-4)
+    assert gg == pytest.approx(fdg, rel=1e-4)
+
+
 def test_rollout_gradient_matches_central_differences_20k():
     """Annulus with ~20k scattered nodes, N_L = 24, P_3, 200 FP64 steps: dL/dtau and dL/dg from
     the adjoint agree with central finite differences of the GPU forward to 1e-4."""
