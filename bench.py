@@ -221,6 +221,54 @@ def _sample_config(workload, ratio=1.0, stencil="own"):
     }
 
 
+def measure_fp64_peak(local, launches=5, target_s=0.25):
+    """The device's FP64 FMA rate, measured: the library's probe of independent FMA chains
+    (mlbm_fp64_fma_rate) sized to about target_s per launch, timed with CUDA events on its
+    stream after two warm-up launches, with the SM clock sampled meanwhile.  Returns the best
+    launch's TFLOP/s and the median SM clock under load."""
+    import torch
+
+    import paper_2306_01525_gb300 as mlbm
+
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    bps = 8
+    sink = torch.zeros(16 * sms, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream(device=dev)
+    iters = 1 << 14
+    with torch.cuda.stream(st):
+        for _ in range(8):  # size the launch
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            mlbm.fp64_fma_rate(iters, bps, sink, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms >= 0.5 * target_s * 1e3:
+                break
+            iters = int(iters * min(16.0, max(2.0, target_s * 1e3 / max(ms, 1e-3))))
+        clocks = ClockSampler(local)
+        clocks.start()
+        rates, by_ctas = [], {}
+        for c in (4, 8, 16):  # CTAs per SM (16 runs as two waves of 8)
+            for it in range(2 + launches):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                flops = mlbm.fp64_fma_rate(iters * bps // c, c, sink, stream=st)
+                e1.record(st)
+                e1.synchronize()
+                if it >= 2:
+                    r = flops / (e0.elapsed_time(e1) * 1e-3) / 1e12
+                    rates.append(r)
+                    by_ctas[c] = max(by_ctas.get(c, 0.0), r)
+        clk = clocks.stop()
+    return {"tflops": max(rates), "tflops_median": statistics.median(rates), "launches": launches,
+            "iters_per_chain_at_8_ctas": iters, "best_by_ctas_per_sm": by_ctas,
+            "sm_mhz_median": clk["sm_mhz"] if clk else None, "clock_reasons": clk["reasons"] if clk else None,
+            "how": "independent FP64 FMA chains (16 per thread, 256 threads x 4, 8 or 16 CTAs per SM), "
+                   "CUDA events on the probe's stream, best of the timed launches"}
+
+
 def annulus_profile(r, g, nu, r1, r2):
     """Analytic azimuthal speed of force-driven flow between two circles, eq. (bch_solution):
     u(r) = -G (r^2 - alpha r + beta / r), G = g / (3 nu), alpha = (r1^2 + r1 r2 + r2^2) / (r1 + r2),
@@ -928,6 +976,8 @@ def run_mlbm(args):
             dist.destroy_process_group()
         return 0
     peak, peak_kind = _peaks()
+    fp64_peak = measure_fp64_peak(local)
+    p64 = fp64_peak["tflops"]
     bpn32 = step_bytes_per_node(K, 4, args.stencil == "nearest")
     achieved = bpn32 * N / (ms_step32 * 1e-3) / 1e9
     default_workload = args.workload == "tgv_large" and args.stencil == "own" and args.ratio == 1.0
@@ -979,7 +1029,9 @@ def run_mlbm(args):
         "fp64": {"value": gnups64, "unit": UNIT, "ms_per_step": ms_step64, "steps": s64,
                  "achieved_gbs": step_bytes_per_node(K, 8, args.stencil == "nearest") * N / (ms_step64 * 1e-3) / 1e9,
                  "bound": "fp64 alu", "achieved_tflops": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12,
-                 "peak_tflops": 1.25, "frac": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12 / 1.25},
+                 "peak_tflops": p64, "peak_source": "measured (fp64_peak)",
+                 "frac": (16 * K + 80) * N / (ms_step64 * 1e-3) / 1e12 / p64},
+        "fp64_peak": fp64_peak,
         "speedup_fp32_vs_fp64": gnups32 / gnups64,
         "fp32_vs_fp64_rel_l2_u": err, "error_steps": args.err_steps,
         "rel_l2_u_vs_analytic": err_an,
@@ -1008,7 +1060,7 @@ def main():
     ap.add_argument("--ratio", type=float, default=1.0, help="dx_ml / h of the main workload")
     ap.add_argument("--leg", default=None,
                     choices=["batched", "annulus", "adjoint", "lattice_lbm", "shan_chen", "paper_sweep", "tgv_small",
-                             "tgv_4096"],
+                             "tgv_4096", "fp64_peak"],
                     help="run only this extra measurement and print it")
     ap.add_argument("--leg-steps", type=int, default=None,
                     help="with --leg: the leg's step count (annulus: its step cap), e.g. for a short ncu capture")
@@ -1030,7 +1082,8 @@ def main():
                 "tgv_4096": lambda: bench_tgv_4096(n or 50),
                 "adjoint": lambda: bench_adjoint(n or 2000), "lattice_lbm": bench_lattice,
                 "shan_chen": bench_shan_chen,
-                "paper_sweep": lambda: bench_paper_sweep("f64")}
+                "paper_sweep": lambda: bench_paper_sweep("f64"),
+                "fp64_peak": lambda: measure_fp64_peak(int(os.environ.get("LOCAL_RANK", "0")))}
         print(json.dumps({args.leg: legs[args.leg]()}), flush=True)
         return 0
     return run_mlbm(args)

@@ -429,6 +429,21 @@ int mlbm_init_adjoint(const mlbm_weights *w, const mlbm_params *params, int dtyp
                       const double *rho, const double *ux, const double *uy, const void *lam0,
                       double *drho, double *dux, double *duy, double *grad, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * mlbm_fp64_fma_rate -- a measurement facility with no counterpart in the paper: enqueues a
+ * kernel of independent FP64 fused multiply-add chains (16 per thread, 256 threads per CTA,
+ * blocks_per_sm CTAs on every SM, iters FMAs per chain) on `stream` and returns through
+ * *flops (host) the floating-point operations it performs (2 per FMA).  Timed by the caller
+ * (CUDA events on the same stream), flops / time is the device's sustained FP64 rate, the
+ * denominator for kernels bound by FP64 arithmetic.
+ *   sink      device, at least blocks_per_sm * (number of SMs) float64 (one sum per CTA,
+ *             written so that the work is not optimised away; caller-owned)
+ *   sink_len  its length; too short returns MLBM_EINVAL with nothing launched
+ * Asynchronous.  Errors: MLBM_EINVAL, MLBM_ECUDA.
+ * ------------------------------------------------------------------------------------- */
+int mlbm_fp64_fma_rate(int64_t iters, int blocks_per_sm, double *sink, int64_t sink_len,
+                       void *stream, double *flops);
+
 #ifdef __cplusplus
 }
 #endif

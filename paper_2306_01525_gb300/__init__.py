@@ -28,7 +28,7 @@ __all__ = [
     "MLBMError", "F32", "F64", "PERIODIC", "ANNULUS", "STENCIL_OWN", "STENCIL_NEAREST",
     "KEEP_W32", "KEEP_W64",
     "lib", "Cloud", "Weights", "build_cloud", "build_weights", "init", "step", "run",
-    "run_until", "moments", "norms", "norms_noalloc", "adjoint_step", "moments_adjoint", "init_adjoint",
+    "run_until", "moments", "norms", "norms_noalloc", "fp64_fma_rate", "adjoint_step", "moments_adjoint", "init_adjoint",
     "lattice_init", "lattice_step", "step_host", "sc_step",
 ]
 
@@ -107,6 +107,7 @@ def lib():
             L.mlbm_moments_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_init_adjoint.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                             _vp, _vp]
+            L.mlbm_fp64_fma_rate.argtypes = [_c_i64, _c_int, _vp, _c_i64, _vp, _vp]
             _lib = L
     return _lib
 
@@ -431,6 +432,18 @@ def norms_noalloc(a, b, c=None, d=None, out=None, stream=None):
                                     _dev_ptr(d, torch.float64, n, "d") if d is not None else None,
                                     n, _dev_ptr(out, torch.float64, 3, "out"), _stream(stream)))
     return out
+
+
+def fp64_fma_rate(iters: int, blocks_per_sm: int, sink, stream=None) -> float:
+    """Enqueue the FP64 FMA rate probe (mlbm_fp64_fma_rate); returns the flops it performs.
+    ``sink`` is a float64 device tensor of at least blocks_per_sm * SMs elements."""
+    import torch
+
+    flops = ctypes.c_double(0.0)
+    _check(lib().mlbm_fp64_fma_rate(int(iters), int(blocks_per_sm),
+                                    _dev_ptr(sink, torch.float64, sink.numel(), "sink"),
+                                    sink.numel(), _stream(stream), ctypes.byref(flops)))
+    return flops.value
 
 
 # ----------------------------------------------------------------------------- lattice LBM

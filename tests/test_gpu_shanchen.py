@@ -119,15 +119,29 @@ def test_fp32_follows_the_fp64_oracle(mode):
     a = _to_stored(oracle.sc_collide_field(f, sidx, W, tau, G), perm, mlbm.F32)
     b = torch.empty_like(a)
     st = oracle.ScStepper(sidx, W, tau, G)
+    # G = -5 lies inside the spinodal region (G_c = -4): the density modes grow exponentially and
+    # carry any rounding with them.  The expected size of FP32 rounding after 40 steps is that of
+    # the FP64 oracle with FP32-sized noise, each stored deviation f - omega rho0 perturbed by up
+    # to 2^-24 of itself every step; the FP32 step rounds several times per population per step
+    # (interpolation, psi, force, collision, storage), so it may exceed that model by a small
+    # factor: bound 10x the model's RMS over three noise realisations (measured about 6x).
+    _, _, om = oracle.d2q9()
+    rngs = [np.random.default_rng(99 + r) for r in range(3)]
+    fns = [f.copy() for _ in rngs]
     for _ in range(40):
         mlbm.sc_step(w, [(tau, 0.0, 1.0)], (G, 1.0), mlbm.F32, a, b)
         a, b = b, a
         f = st.step(f)
+        for r, rng_n in enumerate(rngs):
+            fn = st.step(fns[r])
+            fns[r] = fn + 2.0 ** -24 * np.abs(fn - om[:, None]) * rng_n.uniform(-1.0, 1.0, fn.shape)
     r_o = oracle.moments_field(f)[0]
     r_g = oracle.moments_field(_from_stored(a, perm, mlbm.F32))[0]
-    dev = r_o - r_o.mean()
-    # FP32 rounding of rho (~1e-7, i.e. ~2e-6 of the 5 % deviations) grows with the unstable modes
-    assert np.linalg.norm(r_g - r_o) <= 1e-4 * np.linalg.norm(dev), np.linalg.norm(r_g - r_o) / np.linalg.norm(dev)
+    dev = np.linalg.norm(r_o - r_o.mean())
+    err = np.linalg.norm(r_g - r_o) / dev
+    model = np.sqrt(np.mean([np.sum((oracle.moments_field(fn)[0] - r_o) ** 2) for fn in fns])) / dev
+    assert err <= 10.0 * model, (err, model)
+    assert err <= 1e-5, err
 
 
 def test_lattice_cloud_is_the_lattice_shan_chen_step():
