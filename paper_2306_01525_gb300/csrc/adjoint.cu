@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <string>
 #include <thread>
@@ -100,11 +101,19 @@ struct AdjArgs {
     const int64_t *__restrict__ roff;     // [ntiles] offset of the tile's reverse halo
     const int32_t *__restrict__ rcnt;     // [ntiles] its size
     const int64_t *__restrict__ sbeg;     // [ntiles][B/32] first entry of each 32-row slice
+    const int64_t *__restrict__ cbeg;     // [ntiles][B/32] its first coefficient
     const int32_t *__restrict__ slen;     // [ntiles][B/32] entries per row of the slice
+    const int32_t *__restrict__ nlen;     // [ntiles][B/32][8] nearest rule: entries per direction
     const uint16_t *__restrict__ slot;    // per entry: reverse-halo slot of the reading node
-    const T *__restrict__ coef;           // per entry [8]: its coefficients c_kj
+    const T *__restrict__ coef;           // own rule: per entry [8] coefficients c_kj; nearest
+                                          // rule: per entry its direction's coefficient
     int64_t N;
     int ntiles;
+    // per-segment reduction of the tile sums folded into the pull kernel's last CTA (nullptr:
+    // grad_finalize_kernel does it); done counts finished CTAs and is left at zero
+    unsigned int *done;
+    double *grad;
+    int nseg;
 };
 
 // Transposed collision Jacobian (with d f^eq / d(rho, u)) and transposed bounce-back at node p:
@@ -302,6 +311,23 @@ __device__ __forceinline__ void local_from_next(const AdjArgs<T> &a, int64_t p, 
     adj_collide_node<T>(a, p, lam, rho, ux, uy, inv_tau, mb, mt, own);
 }
 
+// Four consecutive coefficients (16-byte aligned in FP32, two 16-byte loads in FP64), streamed.
+__device__ __forceinline__ void load4(float (&c)[4], const float *p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    c[0] = v.x;
+    c[1] = v.y;
+    c[2] = v.z;
+    c[3] = v.w;
+}
+__device__ __forceinline__ void load4(double (&c)[4], const double *p) {
+    const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    c[0] = v0.x;
+    c[1] = v0.y;
+    c[2] = v1.x;
+    c[3] = v1.y;
+}
+
 // acc += w * m component-wise
 __device__ __forceinline__ void vfma_acc(float4 &acc, const float4 w, const float4 m) {
     acc.x = fmaf(w.x, m.x, acc.x);
@@ -339,8 +365,10 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
     __shared__ double red[2][B / 32];
     const int64_t N = a.N;
     const int b = threadIdx.x;
+    T *shs = reinterpret_cast<T *>(smem_raw);  // nearest rule: [8][U], direction-major
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         const TileDev tile = a.tiles[t];
+        const bool nearest = tile.mode == MLBM_STENCIL_NEAREST;
         const int U = a.rcnt[t];
         const int32_t *__restrict__ rh = a.rhalo + a.roff[t];
         T dtau = T(0), dg = T(0);
@@ -354,19 +382,66 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
 #pragma unroll
                 for (int q = 0; q < NV; ++q) vunpack(mt + q * W, mi[q]);
             }
+            if (nearest) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) vpack(sh[u * NV + q], mt + q * W);
+                for (int k = 0; k < 8; ++k) shs[k * U + u] = mt[k];
+            } else {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) vpack(sh[u * NV + q], mt + q * W);
+            }
         }
         __syncthreads();
-        if (b < tile.count) {
+        if (nearest && b < tile.count) {
+            // the slice's entries direction by direction, each a (slot, coefficient) pair: row m
+            // sums c(i) mut_k(i) over the nodes i whose departure-node stencil for k holds m
+            const int64_t m = tile.begin + a.rowp[(int64_t)t * B + b];
+            const int ws = t * (B / 32) + (b >> 5);
+            const int32_t *__restrict__ nl = a.nlen + (int64_t)ws * 8;
+            // quads of entries: four slots in one 8-byte word, four coefficients contiguous
+            const uint2 *__restrict__ sp = reinterpret_cast<const uint2 *>(a.slot + a.sbeg[ws]) + (b & 31);
+            const T *__restrict__ cp = a.coef + a.cbeg[ws] + 4 * (b & 31);
+#pragma unroll 1
+            for (int k = 0; k < 8; ++k) {
+                const int L4 = nl[k] >> 2;
+                const T *__restrict__ sk = shs + k * U;
+                T acc = T(0);
+                int e = 0;
+                for (; e + 1 < L4; e += 2) {  // two quads per pass
+                    const uint2 s0 = __ldcs(sp + 32 * e), s1 = __ldcs(sp + 32 * (e + 1));
+                    T c0[4], c1[4];
+                    load4(c0, cp + 128 * e);
+                    load4(c1, cp + 128 * (e + 1));
+                    acc = fma(c0[0], sk[s0.x & 0xFFFFu], acc);
+                    acc = fma(c0[1], sk[s0.x >> 16], acc);
+                    acc = fma(c0[2], sk[s0.y & 0xFFFFu], acc);
+                    acc = fma(c0[3], sk[s0.y >> 16], acc);
+                    acc = fma(c1[0], sk[s1.x & 0xFFFFu], acc);
+                    acc = fma(c1[1], sk[s1.x >> 16], acc);
+                    acc = fma(c1[2], sk[s1.y & 0xFFFFu], acc);
+                    acc = fma(c1[3], sk[s1.y >> 16], acc);
+                }
+                if (e < L4) {
+                    const uint2 s0 = __ldcs(sp + 32 * e);
+                    T c0[4];
+                    load4(c0, cp + 128 * e);
+                    acc = fma(c0[0], sk[s0.x & 0xFFFFu], acc);
+                    acc = fma(c0[1], sk[s0.x >> 16], acc);
+                    acc = fma(c0[2], sk[s0.y & 0xFFFFu], acc);
+                    acc = fma(c0[3], sk[s0.y >> 16], acc);
+                }
+                a.lam_prev[(int64_t)(k + 1) * N + m] = acc;
+                sp += (int64_t)32 * L4;
+                cp += (int64_t)128 * L4;
+            }
+        } else if (b < tile.count) {
             const int64_t m = tile.begin + a.rowp[(int64_t)t * B + b];
             const int ws = t * (B / 32) + (b >> 5);
             const int L = a.slen[ws];
             const int64_t q0 = a.sbeg[ws] + (b & 31);
             const uint16_t *__restrict__ sp = a.slot + q0;
             // coefficients in planes per 32-entry row of the slice: vector q of entry (e, lane)
-            // at (sbeg + 32 e) NV + 32 q + lane, so each warp load is 512 contiguous bytes
-            const VT *__restrict__ cp = reinterpret_cast<const VT *>(a.coef) + a.sbeg[ws] * NV + (b & 31);
+            // at cbeg / W + 32 e NV + 32 q + lane, so each warp load is 512 contiguous bytes
+            const VT *__restrict__ cp = reinterpret_cast<const VT *>(a.coef + a.cbeg[ws]) + (b & 31);
             VT acc[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) vzero(acc[q]);
@@ -405,26 +480,83 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
         else
             __syncthreads();
     }
+    if constexpr (kFromNext) {
+        if (a.done) {
+            // the last CTA to finish adds every segment's tile sums to grad: per thread the tiles
+            // t = tid, tid + B, ... in order, then the warps' shuffle trees, then the warps in
+            // order (a fixed order whichever CTA is last)
+            __shared__ int last;
+            if (threadIdx.x == 0) {
+                __threadfence();
+                last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+            }
+            __syncthreads();
+            if (last) {
+                __threadfence();
+                const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+                for (int sg = 0; sg < a.nseg; ++sg) {
+                    double s0 = 0.0, s1 = 0.0;
+                    for (int t = threadIdx.x; t < a.ntiles; t += B)
+                        if (a.tiles[t].seg == sg) {
+                            s0 += __ldcg(a.partials + 2 * t);
+                            s1 += __ldcg(a.partials + 2 * t + 1);
+                        }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                    }
+                    if (lane == 0) {
+                        red[0][warp] = s0;
+                        red[1][warp] = s1;
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        double g0 = 0.0, g1 = 0.0;
+                        for (int q = 0; q < B / 32; ++q) {
+                            g0 += red[0][q];
+                            g1 += red[1][q];
+                        }
+                        a.grad[2 * sg] += g0;
+                        a.grad[2 * sg + 1] += g1;
+                    }
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) *a.done = 0u;
+            }
+        }
+    }
 }
 
 // Coefficients of the sliced entry table: thread (t, b) fills the entries of the tile's b-th
-// row m (slice b / 32, lane b % 32).  The entry at position q reads node i = src[q]: its
-// coefficient for direction k is the weight with which f_k(m) enters fhat_k(i), i.e. c_kj(i)
-// for the member j of the stencil that interpolates (i, k) (the stencil of the departure node
-// L_k(i), or of i itself under the own-node rule) with s_j = m, and 0 if m is not a member.
-// jh[q] >= 0 gives j directly (own-node rows, from the transposed stencil); else it is looked
-// up.  c_kj(i) = W_k[j](i) in the step's precision (FP32: the rounded canonical FP32 shape
-// vectors the forward's FP32 layout is made of), except the FP32 difference form's centre,
-// 1 - sum_{j>=1} W_k[j](i) added up in member order as the forward does.  Padding (src -1) gets
-// zeros.
+// row m (slice b / 32, lane b % 32).  The entry at position q reads node i = src[q], and m is
+// member j = jh[q] of the stencil that interpolates (i, k): the coefficient with which f_k(m)
+// enters fhat_k(i) is c_kj(i) = W_k[j](i) in the step's precision (FP32: the rounded canonical
+// FP32 shape vectors the forward's FP32 layout is made of), except the FP32 difference form's
+// centre, 1 - sum_{j>=1} W_k[j](i) added up in member order as the forward does.  Own-node
+// rule: all eight directions share the entry (m is member j of i's own stencil), coefficients
+// in planes after cbeg.  Nearest-node rule: the slice's entries run direction by direction
+// (nlen per direction, in quads of four entries per lane), one coefficient each at
+// cbeg + (q - sbeg).  Padding (src -1) gets zeros.
+template <typename T>
+__device__ __forceinline__ T adj_coef_of(const SegDev &sd, const double *__restrict__ w64c,
+                                         const float *__restrict__ w32c, int64_t i, int k, int j) {
+    constexpr bool kDev = std::is_same<T, float>::value;
+    const int64_t base = sd.w_off + (int64_t)k * sd.K * sd.n + i;
+    if (!kDev) return (T)w64c[base + (int64_t)j * sd.n];
+    if (j > 0) return (T)w32c[base + (int64_t)j * sd.n];
+    float wsum = 0.f;
+    for (int jj = 1; jj < sd.K; ++jj) wsum += w32c[base + (int64_t)jj * sd.n];
+    return (T)(1.f - wsum);
+}
+
 template <typename T>
 __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, int B, const SegDev *__restrict__ seg,
-                                const uint16_t *__restrict__ rowp, const int64_t *__restrict__ sbeg,
-                                const int32_t *__restrict__ slen, const int32_t *__restrict__ srcs,
-                                const int8_t *__restrict__ jhs, const int32_t *__restrict__ idx,
-                                const int32_t *__restrict__ near, const double *__restrict__ w64c,
-                                const float *__restrict__ w32c, T *__restrict__ coef) {
-    constexpr bool kDev = std::is_same<T, float>::value;
+                                const int64_t *__restrict__ sbeg, const int64_t *__restrict__ cbeg,
+                                const int32_t *__restrict__ slen, const int32_t *__restrict__ nlen,
+                                const int32_t *__restrict__ srcs, const int8_t *__restrict__ jhs,
+                                const double *__restrict__ w64c, const float *__restrict__ w32c,
+                                T *__restrict__ coef) {
     constexpr int W = V<T>::width, NV = 8 / W;
     const int64_t total = (int64_t)ntiles * B;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
@@ -434,40 +566,30 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
         const int L = slen[ws];
         if (L == 0) continue;
         const SegDev sd = seg[tile.seg];
-        const int64_t m = tile.begin + (b < tile.count ? rowp[g] : 0);
+        const int lane = b & 31;
+        if (tile.mode == MLBM_STENCIL_NEAREST) {
+            int64_t kb = sbeg[ws];
+            for (int k = 0; k < 8; ++k) {
+                const int Lk = nlen[(int64_t)ws * 8 + k];
+                for (int e = 0; e < Lk; ++e) {
+                    const int64_t q = kb + 128 * (e >> 2) + 4 * lane + (e & 3);
+                    const int32_t src = b < tile.count ? srcs[q] : -1;
+                    coef[cbeg[ws] + (q - sbeg[ws])] =
+                        src >= 0 ? adj_coef_of<T>(sd, w64c, w32c, src - sd.off, k, jhs[q]) : T(0);
+                }
+                kb += (int64_t)32 * Lk;
+            }
+            continue;
+        }
         for (int e = 0; e < L; ++e) {
-            const int64_t qb = sbeg[ws] + (int64_t)32 * e;  // first entry of the slice's row e
-            const int64_t q = qb + (b & 31);
+            const int64_t q = sbeg[ws] + (int64_t)32 * e + lane;
+            const int32_t src = b < tile.count ? srcs[q] : -1;
             T v[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = T(0);
-            const int32_t src = b < tile.count ? srcs[q] : -1;
-            if (src >= 0) {
-                const int64_t i = src - sd.off;
-                const double *wk = w64c + sd.w_off + i;
-                const float *wk32 = w32c + sd.w_off + i;
-                for (int k = 0; k < 8; ++k) {
-                    int j = jhs[q];
-                    if (j < 0) {  // member of the departure node's stencil equal to m, if any
-                        const int64_t Lk = near ? near[8 * sd.off + (int64_t)k * sd.n + i] - sd.off : i;
-                        for (int jj = 0; jj < sd.K && j < 0; ++jj)
-                            if (idx[sd.idx_off + (int64_t)jj * sd.n + Lk] == m) j = jj;
-                    }
-                    if (j < 0) continue;
-                    if (!kDev) {
-                        v[k] = (T)wk[((int64_t)k * sd.K + j) * sd.n];
-                    } else if (j > 0) {
-                        v[k] = (T)wk32[((int64_t)k * sd.K + j) * sd.n];
-                    } else {
-                        float wsum = 0.f;
-                        for (int jj = 1; jj < sd.K; ++jj) wsum += wk32[((int64_t)k * sd.K + jj) * sd.n];
-                        v[k] = (T)(1.f - wsum);
-                    }
-                }
-            }
-            // planes: vector h (directions h W .. h W + W - 1) of lane b % 32 at (qb NV + 32 h + lane) W
+            for (int k = 0; k < 8; ++k) v[k] = src >= 0 ? adj_coef_of<T>(sd, w64c, w32c, src - sd.off, k, jhs[q]) : T(0);
+            // planes: vector h (directions h W .. h W + W - 1) of the lane at cbeg + (32 e NV + 32 h + lane) W
 #pragma unroll
-            for (int k = 0; k < 8; ++k) coef[(qb * NV + 32 * (k / W) + (b & 31)) * W + k % W] = v[k];
+            for (int k = 0; k < 8; ++k) coef[cbeg[ws] + ((int64_t)32 * e * NV + 32 * (k / W) + lane) * W + k % W] = v[k];
         }
     }
 }
@@ -476,6 +598,7 @@ __global__ void adj_coef_kernel(const TileDev *__restrict__ tiles, int ntiles, i
 // tid adds tiles tid, tid + 1024, ...; then a tree over the threads).  The tile's segment and
 // its partial sums are loaded together, so each pass costs one memory latency.
 constexpr int kFinalizeThreads = 1024;
+constexpr int kFoldSegments = 8;  // up to this many segments the pull kernel reduces the tile sums
 __global__ void __launch_bounds__(kFinalizeThreads) grad_finalize_kernel(const TileDev *__restrict__ tiles, int ntiles,
                                                                           const double *__restrict__ partials,
                                                                           double *__restrict__ grad) {
@@ -578,14 +701,21 @@ __global__ void __launch_bounds__(kThreads) init_adjoint_kernel(
     }
 }
 
+// Scratch of the reverse step: node-major cotangents [N][8] (8 doubles per node at most), the
+// per-tile gradient sums [ntiles][2], then the finished-CTA counter of the pull kernel (zeroed
+// here, left at zero by each launch).
+size_t adj_done_offset(const mlbm_weights *w) { return sizeof(double) * (8 * (size_t)w->N + 2 * (size_t)w->ntiles); }
+
 int ensure_adj_scratch(mlbm_weights *w) {
-    size_t need = sizeof(double) * (8 * (size_t)w->N + 2 * (size_t)w->ntiles);
+    size_t need = adj_done_offset(w) + 16;
     if (w->d_scratch && w->scratch_bytes >= need) return MLBM_OK;
     cudaFree(w->d_scratch);
     w->d_scratch = nullptr;
     cudaError_t e = cudaMalloc(&w->d_scratch, need);
+    if (e == cudaSuccess) e = cudaMemset((char *)w->d_scratch + adj_done_offset(w), 0, 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        cudaFree(w->d_scratch);
         w->d_scratch = nullptr;
         w->scratch_bytes = 0;
         return fail(MLBM_ENOMEM, "adjoint scratch allocation failed");
@@ -658,16 +788,19 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
         }
         std::vector<uint16_t> rowp((size_t)nt * B, 0);
         std::vector<int32_t> slen((size_t)nt * WPT, 0);
+        std::vector<int32_t> nlen((size_t)nt * WPT * 8, 0);  // nearest-rule slices: entries per direction
         std::vector<std::vector<int32_t>> rh(nt);
         std::vector<std::vector<uint16_t>> sl(nt);
         std::vector<std::vector<int32_t>> ps(nt);  // per tile, per position: reading node (-1 padding)
-        std::vector<std::vector<int8_t>> pj(nt);   // per tile, per position: member index hint
+        std::vector<std::vector<int8_t>> pj(nt);   // per tile, per position: member index
         std::vector<int> bad(nt, 0);
         auto work = [&](int t0, int t1) {
             std::vector<int32_t> others;
             std::vector<int> ord;
             std::vector<std::vector<int32_t>> rs;  // per row of the tile: reading nodes
-            std::vector<std::vector<int8_t>> rj;   // and member index hints
+            std::vector<std::vector<int8_t>> rj;   // and member indices
+            std::vector<std::array<int32_t, 9>> rk;  // nearest rule: start of direction k's readers in rs
+            std::vector<std::pair<int32_t, int8_t>> tmp;
             for (int t = t0; t < t1; ++t) {
                 const TileDev &T_ = tiles[t];
                 const SegmentHost &h = w->seg[T_.seg];
@@ -675,6 +808,7 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                 const int64_t m0 = T_.begin;
                 rs.assign(T_.count, {});
                 rj.assign(T_.count, {});
+                rk.assign(T_.count, {});
                 for (int b = 0; b < T_.count; ++b) {
                     const int64_t m = m0 + b;
                     std::vector<int32_t> &R = rs[b];
@@ -683,16 +817,25 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                             R.push_back((int32_t)(h.off + ent[q] % h.n));
                             rj[b].push_back((int8_t)(ent[q] / h.n));
                         }
-                    } else {  // nodes whose departure node for some direction has m in its stencil
-                        for (int32_t q = ptr[m]; q < ptr[m + 1]; ++q) {
-                            const int64_t L = ent[q] % h.n;
-                            for (int k = 0; k < 8; ++k)
+                    } else {
+                        // per direction k, the nodes i whose departure node L_k(i) has m in its
+                        // stencil (as member j), by increasing i: each i at most once per direction
+                        for (int k = 0; k < 8; ++k) {
+                            rk[b][k] = (int32_t)R.size();
+                            tmp.clear();
+                            for (int32_t q = ptr[m]; q < ptr[m + 1]; ++q) {
+                                const int64_t L = ent[q] % h.n;
+                                const int8_t j = (int8_t)(ent[q] / h.n);
                                 for (int32_t r = inv_ptr[T_.seg][k][L]; r < inv_ptr[T_.seg][k][L + 1]; ++r)
-                                    R.push_back(inv_ent[T_.seg][k][r]);
+                                    tmp.emplace_back(inv_ent[T_.seg][k][r], j);
+                            }
+                            std::sort(tmp.begin(), tmp.end());
+                            for (auto &e : tmp) {
+                                R.push_back(e.first);
+                                rj[b].push_back(e.second);
+                            }
                         }
-                        std::sort(R.begin(), R.end());
-                        R.erase(std::unique(R.begin(), R.end()), R.end());
-                        rj[b].assign(R.size(), (int8_t)-1);
+                        rk[b][8] = (int32_t)R.size();
                     }
                 }
                 ord.resize(T_.count);
@@ -718,10 +861,29 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                     if (s_ >= m0 && s_ < m0 + T_.count) return (uint16_t)(s_ - m0);
                     return (uint16_t)(T_.count + (std::lower_bound(others.begin(), others.end(), s_) - others.begin()));
                 };
+                // slices of 32 rows: entry e of lane l at position 32 e + l; under the nearest
+                // rule the directions follow one another, each padded to the slice's longest
+                // rounded up to a multiple of 4, entry e of lane l at 128 (e / 4) + 4 l + e % 4
+                // (four consecutive entries of a lane are one 8-byte slot load and one
+                // 16-byte FP32 coefficient load)
                 int64_t n_ent = 0;
                 for (int ws = 0; ws < WPT; ++ws) {
                     int L = 0;
-                    for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) L = std::max(L, (int)rs[ord[32 * ws + l]].size());
+                    if (!nearest) {
+                        for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l)
+                            L = std::max(L, (int)rs[ord[32 * ws + l]].size());
+                    } else {
+                        for (int k = 0; k < 8; ++k) {
+                            int Lk = 0;
+                            for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
+                                const int r = ord[32 * ws + l];
+                                Lk = std::max(Lk, rk[r][k + 1] - rk[r][k]);
+                            }
+                            Lk = (Lk + 3) & ~3;  // whole quads
+                            nlen[((size_t)t * WPT + ws) * 8 + k] = Lk;
+                            L += Lk;
+                        }
+                    }
                     slen[(size_t)t * WPT + ws] = L;
                     n_ent += 32 * (int64_t)L;
                 }
@@ -734,11 +896,25 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
                     const int L = slen[(size_t)t * WPT + ws];
                     for (int l = 0; l < 32 && 32 * ws + l < T_.count; ++l) {
                         const int r = ord[32 * ws + l];
-                        for (size_t e = 0; e < rs[r].size(); ++e) {
-                            const int64_t q = base + 32 * (int64_t)e + l;
-                            S[q] = slot_of(rs[r][e]);
-                            ps[t][q] = rs[r][e];
-                            pj[t][q] = rj[r][e];
+                        if (!nearest) {
+                            for (size_t e = 0; e < rs[r].size(); ++e) {
+                                const int64_t q = base + 32 * (int64_t)e + l;
+                                S[q] = slot_of(rs[r][e]);
+                                ps[t][q] = rs[r][e];
+                                pj[t][q] = rj[r][e];
+                            }
+                        } else {
+                            int64_t kb = base;
+                            for (int k = 0; k < 8; ++k) {
+                                for (int32_t e = rk[r][k]; e < rk[r][k + 1]; ++e) {
+                                    const int32_t ee = e - rk[r][k];  // quad ee / 4, lane l, place ee % 4
+                                    const int64_t q = kb + 128 * (int64_t)(ee >> 2) + 4 * l + (ee & 3);
+                                    S[q] = slot_of(rs[r][e]);
+                                    ps[t][q] = rs[r][e];
+                                    pj[t][q] = rj[r][e];
+                                }
+                                kb += 32 * (int64_t)nlen[((size_t)t * WPT + ws) * 8 + k];
+                            }
                         }
                     }
                     base += 32 * (int64_t)L;
@@ -754,20 +930,26 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
         }
         for (int t = 0; t < nt; ++t)
             if (bad[t]) return fail(MLBM_EINVAL, "a tile's reverse halo exceeds 65535 nodes (stencils too spread out)");
-        std::vector<int64_t> roff((size_t)nt), sbeg((size_t)nt * WPT);
+        // coefficients: eight per position of an own-rule slice (planes), one per position of
+        // a nearest-rule slice (its direction's)
+        std::vector<int64_t> roff((size_t)nt), sbeg((size_t)nt * WPT), cbeg((size_t)nt * WPT);
         std::vector<int32_t> rcnt((size_t)nt), rall, srcs;
         std::vector<uint16_t> slots;
         std::vector<int8_t> jhs;
         int rmax = 0;
+        int64_t cbase = 0;
         for (int t = 0; t < nt; ++t) {
             roff[t] = (int64_t)rall.size();
             rcnt[t] = (int32_t)rh[t].size();
             rmax = std::max(rmax, rcnt[t]);
             rall.insert(rall.end(), rh[t].begin(), rh[t].end());
             int64_t base = (int64_t)slots.size();
+            const bool nearest = tiles[t].mode == MLBM_STENCIL_NEAREST;
             for (int ws = 0; ws < WPT; ++ws) {
                 sbeg[(size_t)t * WPT + ws] = base;
+                cbeg[(size_t)t * WPT + ws] = cbase;
                 base += 32 * (int64_t)slen[(size_t)t * WPT + ws];
+                cbase += 32 * (int64_t)slen[(size_t)t * WPT + ws] * (nearest ? 1 : 8);
             }
             slots.insert(slots.end(), sl[t].begin(), sl[t].end());
             srcs.insert(srcs.end(), ps[t].begin(), ps[t].end());
@@ -778,13 +960,16 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
             std::vector<int8_t>().swap(pj[t]);
         }
         w->adj_positions = (int64_t)slots.size();
+        w->adj_coefs = cbase;
         w->adj_rmax = rmax;
         if ((rc = upload_vec(&w->d_adj_rowp, rowp, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_rhalo, rall, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_roff, roff, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_rcnt, rcnt, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_sbeg, sbeg, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_cbeg, cbeg, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_slen, slen, "adjoint tables")) ||
+            (rc = upload_vec(&w->d_adj_nlen, nlen, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_slot, slots, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_src, srcs, "adjoint tables")) ||
             (rc = upload_vec(&w->d_adj_jh, jhs, "adjoint tables")))
@@ -793,15 +978,15 @@ int ensure_adj_tables(mlbm_weights *w, cudaStream_t st) {
     const int i = std::is_same<T, float>::value ? 0 : 1;
     if (w->d_adj_coef[i]) return MLBM_OK;
     if (i == 0 && !w->d_w32c) return fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
-    if (cudaMalloc(&w->d_adj_coef[i], sizeof(T) * 8 * (size_t)std::max<int64_t>(1, w->adj_positions)) != cudaSuccess) {
+    if (cudaMalloc(&w->d_adj_coef[i], sizeof(T) * (size_t)std::max<int64_t>(1, w->adj_coefs)) != cudaSuccess) {
         cudaGetLastError();
         w->d_adj_coef[i] = nullptr;
         return fail(MLBM_ENOMEM, "adjoint table allocation failed");
     }
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nt * B + 255) / 256, 65536));
-    adj_coef_kernel<T><<<grid, 256, 0, st>>>(w->d_tiles, nt, B, w->d_seg, w->d_adj_rowp, w->d_adj_sbeg, w->d_adj_slen,
-                                             w->d_adj_src, w->d_adj_jh, w->d_idx, w->d_near, w->d_w64,
-                                             w->d_w32c, (T *)w->d_adj_coef[i]);
+    adj_coef_kernel<T><<<grid, 256, 0, st>>>(w->d_tiles, nt, B, w->d_seg, w->d_adj_sbeg, w->d_adj_cbeg, w->d_adj_slen,
+                                             w->d_adj_nlen, w->d_adj_src, w->d_adj_jh, w->d_w64, w->d_w32c,
+                                             (T *)w->d_adj_coef[i]);
     return cuda_check_step(cudaGetLastError(), "adjoint table launch");
 }
 
@@ -865,14 +1050,21 @@ int adjoint_step_t(mlbm_weights *w, const void *s_prev, const void *s_next, cons
     a.roff = w->d_adj_roff;
     a.rcnt = w->d_adj_rcnt;
     a.sbeg = w->d_adj_sbeg;
+    a.cbeg = w->d_adj_cbeg;
     a.slen = w->d_adj_slen;
+    a.nlen = w->d_adj_nlen;
     a.slot = w->d_adj_slot;
     a.coef = (const T *)w->d_adj_coef[kDev ? 0 : 1];
     a.N = w->N;
     a.ntiles = w->ntiles;
+    // few segments: the pull kernel's last CTA reduces the tile sums (one launch fewer)
+    const bool fold = s_next && w->nseg <= kFoldSegments;
+    a.done = fold ? (unsigned int *)((char *)w->d_scratch + adj_done_offset(w)) : nullptr;
+    a.grad = grad;
+    a.nseg = w->nseg;
     rc = with_tile_nodes(w->tile_nodes, [&](auto Bc) { return launch_reverse<T, decltype(Bc)::value>(w, a, st); });
     if (rc) return rc;
-    grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
+    if (!fold) grad_finalize_kernel<<<w->nseg, kFinalizeThreads, 0, st>>>(w->d_tiles, w->ntiles, a.partials, grad);
     return cuda_check_step(cudaGetLastError(), "adjoint launch");
 }
 

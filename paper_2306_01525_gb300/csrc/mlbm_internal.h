@@ -196,19 +196,23 @@ struct mlbm_weights_impl {
     // length ([ntiles][B] offsets), its reverse halo (own nodes, then every other node that reads
     // one of them, sorted; offset and size per tile), per 32-row slice of that order its first
     // entry and entries per row ([ntiles][B/32]), per entry the reading node's reverse-halo slot,
-    // and the entries' coefficients in FP32 / FP64 ([entries][8])
+    // and the entries' coefficients in FP32 / FP64 (own-node rule: eight per entry; nearest-node
+    // rule: the slice's entries are listed direction by direction, one coefficient each)
     uint16_t *d_adj_rowp = nullptr;
     int32_t *d_adj_rhalo = nullptr;
     int64_t *d_adj_roff = nullptr;
     int32_t *d_adj_rcnt = nullptr;
     int64_t *d_adj_sbeg = nullptr;
+    int64_t *d_adj_cbeg = nullptr;  // [ntiles][B/32] first coefficient of each slice
     int32_t *d_adj_slen = nullptr;
+    int32_t *d_adj_nlen = nullptr;  // [ntiles][B/32][8] nearest-rule slices: entries per direction
     uint16_t *d_adj_slot = nullptr;
     int32_t *d_adj_src = nullptr;  // per entry: reading node (stored position; -1 padding)
-    int8_t *d_adj_jh = nullptr;    // per entry: row node's member index in the reader's stencil, -1: find it
+    int8_t *d_adj_jh = nullptr;    // per entry: row node's member index in the reader's stencil
     int32_t *d_near = nullptr;     // nearest-node clouds: per segment [8][n] departure nodes (stored positions)
     void *d_adj_coef[2] = {nullptr, nullptr};
     int64_t adj_positions = 0;
+    int64_t adj_coefs = 0;
     int adj_rmax = 0;  // largest reverse halo
     // Shan-Chen steps: [nseg][2] (G, rho_psi) in FP64 then FP32, and the psi scratch [N]
     double *d_sc = nullptr;

@@ -566,7 +566,9 @@ void free_weights(mlbm_weights *w) {
     cudaFree(w->d_adj_roff);
     cudaFree(w->d_adj_rcnt);
     cudaFree(w->d_adj_sbeg);
+    cudaFree(w->d_adj_cbeg);
     cudaFree(w->d_adj_slen);
+    cudaFree(w->d_adj_nlen);
     cudaFree(w->d_adj_slot);
     cudaFree(w->d_adj_src);
     cudaFree(w->d_adj_jh);
