@@ -129,3 +129,52 @@ def test_largest_cloud_one_step_sampled_parity():
         r_o, u_o, v_o = oracle.moments(f1n)
         m = got[:, inv[i]]
         assert abs(m[0] - r_o) < 1e-7 and abs(m[1] - u_o) < 1e-8 and abs(m[2] - v_o) < 1e-8, (i, m, r_o, u_o, v_o)
+
+
+def test_512_node_tiles_fp32_run_and_fp64_steps_against_oracle():
+    """The 512-node tile kernels (the benchmark's launch configuration) against the oracle over
+    whole runs, at the smallest cloud of the large recipe that selects them (at least four
+    512-node tiles per SM): 560^2 jittered nodes, seed 3, N_L 30, P_4, the oracle's shape vectors
+    uploaded.  FP64: three steps, each within 1e-12 of the oracle's step.  FP32: 200 steps
+    within 1e-6 relative L2 of the velocity of the FP64 oracle."""
+    n_side = 560
+    n = n_side * n_side
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert -(-n // 512) >= 4 * sms  # the tile-size rule picks 512-node tiles for this cloud
+    xy = mi.jittered_lattice(n_side, 0.3, seed=SEED)
+    dx = 1.0 / n_side
+    cloud = mlbm.build_cloud(xy, dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=K, degree=DEG, dx_ml=dx),
+                             device=True)
+    w = mlbm.build_weights(cloud)
+    sidx, W = oracle.weights(xy, K, DEG, dx, box=(1.0, 1.0))
+    w.upload(W[1:], sidx[1].astype(np.int32))
+    perm = cloud.perm()
+    rho, u, v = mi.tgv_initial(xy, U0)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:0")
+    params = [(TAU, 0.0, 1.0)]
+    st = oracle.Stepper(sidx, W, TAU)
+    f_or = oracle.init_equilibrium(rho, u, v)
+    # FP64, step by step (the library holds f^post = C(f))
+    a = torch.empty(9 * n, dtype=torch.float64, device="cuda:0")
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F64, t(rho), t(u), t(v), a)
+    for it in range(3):
+        mlbm.step(w, params, mlbm.F64, a, b)
+        a, b = b, a
+        f_or = st.step(f_or)
+        post = oracle.collide_field(f_or, TAU)
+        got = np.empty_like(post)
+        got[:, perm] = a.view(9, n).cpu().numpy()
+        assert np.max(np.abs(got - post)) <= 1e-12 * np.max(np.abs(post)), it
+    del a, b
+    # FP32, 200 steps
+    f_or = st.run(f_or, 197)
+    _, u_o, v_o = oracle.moments_field(f_or)
+    a = torch.empty(9 * n, dtype=torch.float32, device="cuda:0")
+    b = torch.empty_like(a)
+    mlbm.init(w, params, mlbm.F32, t(rho), t(u), t(v), a)
+    res = mlbm.run(w, params, mlbm.F32, a, b, 200)
+    _, ug, vg = mlbm.moments(w, params, mlbm.F32, res)
+    ug, vg = ug.cpu().numpy(), vg.cpu().numpy()
+    err = np.sqrt(np.sum((ug - u_o) ** 2 + (vg - v_o) ** 2) / np.sum(u_o ** 2 + v_o ** 2))
+    assert err <= 1e-6, err
