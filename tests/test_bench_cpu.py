@@ -24,6 +24,14 @@ def test_step_bytes_per_node_counts_each_stream_once():
     assert bench.step_bytes_per_node(30, 4, nearest=True) == 8 * 29 * 4 + 8 * 30 * 4 + 72
 
 
+def test_roofline_bytes_follow_the_scope_table_count():
+    # shared stencil, K entries per direction and K indices: 36 K + 72 (FP32), 68 K + 144 (FP64)
+    assert bench.survey_bytes_per_node(30, 4) == 36 * 30 + 72 == 1152
+    assert bench.survey_bytes_per_node(30, 8) == 68 * 30 + 144 == 2184
+    # the FP32 kernel's own count is 36 bytes less (no centre weight, no centre index)
+    assert bench.survey_bytes_per_node(30, 4) - bench.step_bytes_per_node(30, 4) == 36
+
+
 def test_adjoint_and_shan_chen_bytes_per_node():
     K = 24
     # reverse step: the forward's weights and indices once, s_next and lam_next in, lam_prev out
