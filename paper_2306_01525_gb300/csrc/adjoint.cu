@@ -354,7 +354,11 @@ __device__ __forceinline__ void vfma_acc(double2 &acc, const double2 w, const do
 //      sbeg + 32 e + l, rows padded to the slice's longest with slot 0 and zero coefficients;
 //      the coefficients in planes, vector q of the 32 lanes' entries contiguous), so every
 //      warp load is a contiguous run, and the gathered cotangents come from shared memory.
-//      No atomics: deterministic.
+//      Nearest-node tiles: the cotangents are staged direction-major ([k][slot]) and each row
+//      sums, direction by direction, its (slot, coefficient) entries, four per lane contiguous;
+//   3. with the per-segment reduction folded in (a.done), the last CTA to finish adds every
+//      segment's tile sums to grad in a fixed order.
+//      No atomics in the sums: deterministic.
 template <typename T, int B, bool kFromNext>
 __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
     using VT = typename V<T>::type;
