@@ -199,8 +199,16 @@ int mlbm_weights_info(const mlbm_weights *w, int64_t *n_nodes, int *nseg);
  * in mlbm_cloud_stencil, node i in original segment order.  Needs MLBM_KEEP_W64. */
 int mlbm_weights_download(const mlbm_weights *w, int seg, double *W);
 
+/* Copy the FP32 shape vectors the FP32 step uses to the host: W (host, float32, the layout of
+ * mlbm_weights_download).  Entries j >= 1 are the FP64 values rounded one by one so that the
+ * reproduction of the monomials of degree 1..min(d, 6) about the stencil centre (Sec. 2.2,
+ * the P^T block of eq. rbf_interp_set_augmented) holds as closely as FP32 allows, each within
+ * 2^-12 max|w| of its FP64 value; entry 0 (the centre, which the FP32 difference form does not
+ * read) is the FP64 value rounded to nearest.  Needs MLBM_KEEP_W32. */
+int mlbm_weights_download_f32(const mlbm_weights *w, int seg, float *W);
+
 /* Replace the shape vectors of segment seg with caller-supplied FP64 values (same layout as
- * mlbm_weights_download); both the FP64 and the FP32 copies held are overwritten.  idx
+ * mlbm_weights_download); the FP64 copy and the FP32 copy rounded from it are overwritten.  idx
  * (host, [N_L][n_seg] int32, layout of mlbm_cloud_stencil) must equal the library's own
  * stencil, else MLBM_EINVAL and nothing changes.  Synchronous; the adjoint's coefficients,
  * if built, are discarded (after a device synchronisation) and rebuilt from the new shape

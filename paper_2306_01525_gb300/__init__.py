@@ -91,6 +91,7 @@ def lib():
             L.mlbm_weights_free.restype = None
             L.mlbm_weights_info.argtypes = [_vp, _vp, _vp]
             L.mlbm_weights_download.argtypes = [_vp, _c_int, _vp]
+            L.mlbm_weights_download_f32.argtypes = [_vp, _c_int, _vp]
             L.mlbm_weights_upload.argtypes = [_vp, _c_int, _vp, _vp]
             L.mlbm_init.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp, _vp]
             L.mlbm_step.argtypes = [_vp, _vp, _c_int, _vp, _vp, _vp, _vp]
@@ -278,6 +279,15 @@ class Weights:
         K = int(self.segments[seg]["k"])
         out = np.zeros((8, K, ns), np.float64)
         _check(lib().mlbm_weights_download(self._h, seg, out.ctypes.data))
+        return out
+
+    def download_f32(self, seg=0):
+        """FP32 shape vectors the FP32 step uses (rounded to keep the polynomial reproduction),
+        [8][K][n_seg] float32, original order."""
+        ns = int(self.offsets[seg + 1] - self.offsets[seg])
+        K = int(self.segments[seg]["k"])
+        out = np.zeros((8, K, ns), np.float32)
+        _check(lib().mlbm_weights_download_f32(self._h, seg, out.ctypes.data))
         return out
 
     def upload(self, W, idx, seg=0):

@@ -986,6 +986,23 @@ int mlbm_weights_download(const mlbm_weights *w, int seg, double *W) {
     return MLBM_OK;
 }
 
+int mlbm_weights_download_f32(const mlbm_weights *w, int seg, float *W) {
+    if (!w || !W) return fail(MLBM_EINVAL, "NULL argument");
+    if (seg < 0 || seg >= w->nseg) return fail(MLBM_EINVAL, "segment out of range");
+    if (!w->d_w32c) return fail(MLBM_EINVAL, "weights built without MLBM_KEEP_W32");
+    const SegmentHost &h = w->seg[seg];
+    size_t cnt = (size_t)8 * h.K * h.n;
+    std::vector<float> tmp(cnt);
+    int rc = cuda_check(cudaMemcpy(tmp.data(), w->d_w32c + h.w_off, cnt * sizeof(float), cudaMemcpyDeviceToHost),
+                        "download FP32 weights");
+    if (rc) return rc;
+    for (int64_t p = 0; p < h.n; ++p) {
+        int64_t io = w->perm[h.off + p] - h.orig_off;
+        for (int64_t r = 0; r < (int64_t)8 * h.K; ++r) W[r * h.n + io] = tmp[r * h.n + p];
+    }
+    return MLBM_OK;
+}
+
 int mlbm_weights_upload(mlbm_weights *w, int seg, const double *W, const int32_t *idx) {
     if (!w || !W || !idx) return fail(MLBM_EINVAL, "NULL argument");
     if (seg < 0 || seg >= w->nseg) return fail(MLBM_EINVAL, "segment out of range");
