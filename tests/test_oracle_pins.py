@@ -179,6 +179,16 @@ def test_residual_hand_computed():
     assert oracle.residual(u_old, v_old, u_new, v_new) == pytest.approx(np.sqrt(2.0 / 8.0), rel=1e-15)
 
 
+def test_l2_norm_hand_computed():
+    """eq. (L2norm): sqrt(sum (u - u_true)^2) / sqrt(sum u_true^2).  u = (3, 0, 4) against
+    (1, 2, 2): differences (2, -2, 2) give sqrt(12) over sqrt(9), i.e. 2/sqrt(3); without the
+    square roots it would be 4/3, normalised by the computed field sqrt(12/25)."""
+    u = np.array([3.0, 0.0, 4.0])
+    ut = np.array([1.0, 2.0, 2.0])
+    assert oracle.l2_norm(u, ut) == pytest.approx(2.0 / np.sqrt(3.0), rel=1e-15)
+    assert oracle.l2_norm(ut, ut) == 0.0
+
+
 def test_speed_rel_error_hand_computed():
     """eq. (vmag_error): e_i = | |U_i| - |U_i,true| | / |U_i,true| with |U| = sqrt(u^2 + v^2).
     Node 0: |U| = 5 against a true speed of 4 gives 1/4 (dividing by the computed speed would
