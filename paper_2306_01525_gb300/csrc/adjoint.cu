@@ -500,11 +500,25 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
                 for (int sg = 0; sg < a.nseg; ++sg) {
                     double s0 = 0.0, s1 = 0.0;
-                    for (int t = threadIdx.x; t < a.ntiles; t += B)
-                        if (a.tiles[t].seg == sg) {
-                            s0 += __ldcg(a.partials + 2 * t);
-                            s1 += __ldcg(a.partials + 2 * t + 1);
+                    // eight tiles' segments and sums loaded before any is added (one memory
+                    // latency per eight tiles, not two per tile)
+                    for (int t0 = threadIdx.x; t0 < a.ntiles; t0 += 8 * B) {
+                        int sgv[8];
+                        double2 pv[8];
+#pragma unroll
+                        for (int r = 0; r < 8; ++r) {
+                            const int t = t0 + r * B;
+                            sgv[r] = t < a.ntiles ? a.tiles[t].seg : -1;
+                            pv[r] = t < a.ntiles ? __ldcg(reinterpret_cast<const double2 *>(a.partials) + t)
+                                                 : make_double2(0.0, 0.0);
                         }
+#pragma unroll
+                        for (int r = 0; r < 8; ++r)
+                            if (sgv[r] == sg) {
+                                s0 += pv[r].x;
+                                s1 += pv[r].y;
+                            }
+                    }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
