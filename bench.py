@@ -511,10 +511,11 @@ def bench_adjoint(steps: int = 2000):
         for _ in range(reps):
             flush.zero_()
             torch.sum(clean, dim=0, out=sink)
-            # a short device-side delay (about 50 us at 2 GHz) before the start event, so that
-            # the host has issued the call's launches before the device reaches the event and
-            # the interval holds device time only, not the host's argument handling
-            torch.cuda._sleep(100_000)
+            # a device-side delay (about 200 us at 2 GHz) before the start event, so that the
+            # host has issued the call's launches before the device reaches the event and the
+            # interval holds device time only, not the host's argument handling (about 30 us for
+            # the reverse step); with 50 us the reverse step read 4 us longer
+            torch.cuda._sleep(400_000)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
