@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(128) round32_kernel(const SegDev *__restrict__
     float px[kMaxK], py[kMaxK];
     double wv[kMaxK];
     unsigned char ord[kMaxK];
-    float G[P], Lc[P], R[M], a[M], v[M];
+    float G[P], Lc[P], Li[M], R[M], a[M], v[M];
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < 8 * n; g += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(g / n);  // direction k + 1
         const int64_t i = g - (int64_t)k * n;
@@ -426,21 +426,27 @@ __global__ void __launch_bounds__(128) round32_kernel(const SegDev *__restrict__
         const double bound = wmax * 0x1p-12;
         float *out = w32c + sd.w_off + (int64_t)k * K * n + i;
         out[0] = (float)wk[0];  // centre: not read by the FP32 difference form
+        bool ok = true;
         for (int p = 0; p < nw; ++p) {
             const int j = ord[p];
             mono(j, a);
-            // Cholesky of G + lambda I, then v = (G + lambda I)^{-1} R
-            bool ok = true;
-            for (int r = 0, er = 0; r < M; er += ++r) {
-                for (int q = 0; q <= r; ++q) {
-                    const int eq = q * (q + 1) / 2;
-                    float t = G[er + q] + (q == r ? kRoundLambda : 0.f);
-                    for (int u = 0; u < q; ++u) t = fmaf(-Lc[er + u], Lc[eq + u], t);
-                    if (q == r) {
-                        ok = ok && t > 0.f;
-                        Lc[er + r] = t > 0.f ? sqrtf(t) : 1.f;
-                    } else {
-                        Lc[er + q] = t / Lc[eq + q];
+            // Cholesky of G + lambda I (refactorised every second entry: the factor of the Gram
+            // matrix that still holds the previous entry serves the next one), then
+            // v = (G + lambda I)^{-1} R; the diagonal is kept as reciprocals
+            if ((p & 1) == 0) {
+                ok = true;
+                for (int r = 0, er = 0; r < M; er += ++r) {
+                    for (int q = 0; q <= r; ++q) {
+                        const int eq = q * (q + 1) / 2;
+                        float t = G[er + q] + (q == r ? kRoundLambda : 0.f);
+                        for (int u = 0; u < q; ++u) t = fmaf(-Lc[er + u], Lc[eq + u], t);
+                        if (q == r) {
+                            ok = ok && t > 0.f;
+                            Li[r] = t > 0.f ? 1.f / sqrtf(t) : 1.f;
+                            Lc[er + r] = 1.f;
+                        } else {
+                            Lc[er + q] = t * Li[q];
+                        }
                     }
                 }
             }
@@ -449,12 +455,12 @@ __global__ void __launch_bounds__(128) round32_kernel(const SegDev *__restrict__
                 for (int r = 0, er = 0; r < M; er += ++r) {
                     float t = R[r];
                     for (int q = 0; q < r; ++q) t = fmaf(-Lc[er + q], v[q], t);
-                    v[r] = t / Lc[er + r];
+                    v[r] = t * Li[r];
                 }
                 for (int r = M - 1; r >= 0; --r) {
                     float t = v[r];
                     for (int q = r + 1; q < M; ++q) t = fmaf(-Lc[q * (q + 1) / 2 + r], v[q], t);
-                    v[r] = t / Lc[r * (r + 1) / 2 + r];
+                    v[r] = t * Li[r];
                 }
                 float dot = 0.f;
 #pragma unroll
