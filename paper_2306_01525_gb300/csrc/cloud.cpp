@@ -401,7 +401,7 @@ extern "C" {
 
 const char *mlbm_last_error(void) { return g_err.c_str(); }
 
-int mlbm_abi_version(void) { return 5; }
+int mlbm_abi_version(void) { return 6; }
 
 int mlbm_build_cloud(const double *xy, int64_t n, const mlbm_segment_desc *segs,
                      const int64_t *seg_offsets, int nseg, mlbm_cloud **out) {

@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_abi_version():
-    assert mlbm.lib().mlbm_abi_version() == 5
+    assert mlbm.lib().mlbm_abi_version() == 6
 
 
 def _periodic(k, deg, dx):
