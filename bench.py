@@ -229,7 +229,7 @@ def _sample_config(workload, ratio=1.0, stencil="own"):
     }
 
 
-def measure_fp64_peak(local, launches=5, target_s=0.25):
+def measure_fp64_peak(local, launches=5, target_s=0.05):
     """The device's FP64 FMA rate, measured: the library's probe of independent FMA chains
     (mlbm_fp64_fma_rate) sized to about target_s per launch, timed with CUDA events on its
     stream after two warm-up launches, with the SM clock sampled meanwhile.  Returns the best
