@@ -406,6 +406,35 @@ def test_adjoint_step_batched_segments_match_finite_differences(taus):
             assert float(grad[2 * seg + c]) == pytest.approx(float(f), rel=1e-6), (seg, c)
 
 
+def test_adjoint_step_many_segments_match_finite_differences():
+    """Ten segments in one weights object: more than the pull kernel reduces itself, so the
+    per-segment gradient sums go through the separate reduction launch; each segment's dL/dtau
+    and dL/dg against central differences (from the forward's next state, FP64)."""
+    parts, segs = [], []
+    for s in range(10):
+        ns = 10 + s % 4
+        parts.append(mi.jittered_lattice(ns, 0.3, seed=140 + s))
+        segs.append(dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=9 + (s % 3), degree=2, dx_ml=0.6 / ns))
+    offs = np.cumsum([0] + [p.shape[1] for p in parts])
+    xy = np.concatenate(parts, axis=1)
+    w = mlbm.build_weights(mlbm.build_cloud(xy, segs, offs))
+    params = [(0.75 + 0.05 * s, 1e-5 * (s - 4), 1.0) for s in range(10)]
+    st = _rand_state(w, params, xy, seed=41)
+    rng = np.random.default_rng(42)
+    lam = _t(rng.standard_normal(9 * w.n))
+    lam_prev = torch.empty_like(lam)
+    grad = torch.zeros(20, dtype=torch.float64, device=DEV)
+    mlbm.adjoint_step(w, params, mlbm.F64, st, lam, lam_prev, grad, s_next=_step(w, params, st))
+    for seg in (0, 3, 9):
+        for c in (0, 1):
+            lo, hi = [list(p) for p in params], [list(p) for p in params]
+            lo[seg][c] -= 1e-6
+            hi[seg][c] += 1e-6
+            f = (torch.dot(lam, _step(w, [tuple(p) for p in hi], st)) -
+                 torch.dot(lam, _step(w, [tuple(p) for p in lo], st))) / 2e-6
+            assert float(grad[2 * seg + c]) == pytest.approx(float(f), rel=1e-6), (seg, c)
+
+
 def test_upload_after_adjoint_rebuilds_its_coefficients():
     """Shape vectors uploaded after a reverse step replace the adjoint's transposed
     coefficients too: the next reverse step equals that of a fresh weights object holding the
