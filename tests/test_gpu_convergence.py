@@ -100,6 +100,47 @@ def test_annulus_steady_state_follows_analytic_profile():
     assert ur_f < 0.02, ur_f
 
 
+def test_interpolation_with_gpu_shape_vectors_converges_above_second_order():
+    """Fig. interp_test with the GPU's own shape vectors: f = 0.01 sin(2 pi x) cos(2 pi y) at the
+    Lagrangian points of dx_ml = 1/10, each interpolated in the stencil of its nearest Eulerian
+    node (Sec. 2.3), N_L = 25, on clouds refined from 10^2 to 80^2 nodes: the error falls faster
+    than second order for P_2 and faster than fourth order for P_4 (the paper's guide slopes are
+    2 and 5), P_4 below P_2, and each error equals the one the oracle's shape vectors give to
+    1e-6 of itself."""
+    fun = lambda x, y: 0.01 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    ex = [1, 0, -1, 0, 1, -1, -1, 1]
+    ey = [0, 1, 0, -1, 1, 1, -1, -1]
+    sides = (10, 20, 40, 80)
+    errs = {2: [], 4: []}
+    for deg in (2, 4):
+        for n_side in sides:
+            xy = mi.jittered_lattice(n_side, 0.3, seed=n_side)
+            seg = dict(geometry=mlbm.PERIODIC, lx=1.0, ly=1.0, k=25, degree=deg, dx_ml=0.1,
+                       stencil_mode=mlbm.STENCIL_NEAREST)
+            cloud = mlbm.build_cloud(xy, seg)
+            w = mlbm.build_weights(cloud)
+            Wg = w.download(0)
+            st, dep = cloud.stencil(0), cloud.departure_nodes(0)
+            fv = fun(xy[0], xy[1])
+            num = den = 0.0
+            for k in range(8):
+                interp = np.sum(Wg[k] * fv[st[:, dep[k]]], axis=0)
+                exact = fun(xy[0] - ex[k] * 0.1, xy[1] - ey[k] * 0.1)
+                num += np.sum((interp - exact) ** 2)
+                den += np.sum(exact ** 2)
+            errs[deg].append(np.sqrt(num / den))
+            if n_side <= 40:  # the oracle's shape vectors give the same error
+                sidx, W = oracle.weights(xy, 25, deg, 0.1, box=(1.0, 1.0), mode="paper")
+                no = sum(np.sum((np.sum(W[k + 1] * fv[sidx[k + 1]], axis=0) -
+                                 fun(xy[0] - ex[k] * 0.1, xy[1] - ey[k] * 0.1)) ** 2) for k in range(8))
+                assert abs(np.sqrt(no / den) - errs[deg][-1]) <= 1e-6 * errs[deg][-1], (deg, n_side)
+    for deg, least in ((2, 2.0), (4, 4.0)):  # measured 2.5-3.0 and 4.8-5.1
+        e = np.array(errs[deg])
+        slopes = np.log(e[:-1] / e[1:]) / np.log(2.0)
+        assert slopes.min() > least, (deg, e, slopes)
+    assert all(a < b for a, b in zip(errs[4], errs[2])), errs
+
+
 def _annulus_run(h, K, deg, dx, tau=1.0, g=1e-6, max_steps=500000, chunk=10000, seed=2):
     """Steady annulus run on a cloud of spacing h: returns the L2 error of the speed against
     eq. (bch_solution) and the last per-step residual."""
