@@ -87,8 +87,51 @@ __device__ __forceinline__ void collide(T (&s)[9], T rho_ref, T inv_tau, T gx, T
 // every step (a drift of order 1e-8 per step).  The non-equilibrium part n = fhat - f^eq
 // is therefore projected onto zero mass and momentum with exact operations (its mass is taken
 // from n_0, half of its x / y momentum from each of n_1, n_3 / n_2, n_4) before relaxing.
+//
+// The stored result is then rounded so that its mass and momentum are those of the collision in
+// exact arithmetic (fhat's mass, fhat's momentum plus g) as closely as FP32 allows: the FP32
+// updates leave a residual R = (sum D, sum e_x D - g_x, sum e_y D - g_y) of the changes
+// D_k = s'_k - s_k, and the populations are re-rounded one at a time in the fixed order
+// 1, 2, 3, 4, 5, 6, 7, 8, 0 at s'_k + delta_k, delta_k = -c_k . R, where c_k = (G + 0.01 I)^{-1}
+// a_k is the minimum-norm feedback for a_k = (1, e_kx, e_ky) over the populations not yet
+// re-rounded (G the sum of their a a^T; the rest population, last, takes the remaining mass).
+// The rounding of the conserved moments, which the collision does not damp, would otherwise
+// accumulate in the slowly decaying long-wave modes of large clouds.
+__device__ __forceinline__ void conserve_rounding(float (&s)[9], const float (&s_in)[9], float gx, float gy) {
+    constexpr int kOrder[9] = {1, 2, 3, 4, 5, 6, 7, 8, 0};
+    constexpr float kC[9][3] = {{0.110987791f, 0.166389351f, 0.0f},
+                                {0.128034429f, 0.0255557742f, 0.166389351f},
+                                {0.121074514f, -0.175434229f, 0.0241665696f},
+                                {0.137752876f, 0.0f, -0.172105214f},
+                                {0.199600798f, 0.249376559f, 0.249376559f},
+                                {0.331677695f, -0.08436278f, 0.414390337f},
+                                {0.00487781084f, -0.497512438f, -0.492658895f},
+                                {0.0049017205f, 0.495073771f, -0.495073771f},
+                                {0.99009901f, 0.0f, 0.0f}};
+    float d[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) d[k] = s[k] - s_in[k];
+    float r0 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    float rx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]) - gx;
+    float ry = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]) - gy;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const int k = kOrder[p];
+        const float delta = -((kC[p][0] * r0 + kC[p][1] * rx) + kC[p][2] * ry);
+        const float v = s[k] + delta;
+        const float dv = v - s[k];
+        s[k] = v;
+        r0 += dv;
+        rx += float(ex_of(k)) * dv;
+        ry += float(ey_of(k)) * dv;
+    }
+}
+
 __device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, float inv_tau, float gx, float gy,
                                                   float &rho, float &ux, float &uy) {
+    float s_in[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s_in[k] = s[k];
     float drho;
     moments_of(s, rho_ref, drho, rho, ux, uy);
     const float usq15 = 1.5f * (ux * ux + uy * uy);
@@ -108,6 +151,7 @@ __device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, 
         const float force = omega_of<float>(k) * 3.0f * (float(ex_of(k)) * gx + float(ey_of(k)) * gy);
         s[k] = s[k] - ne[k] * inv_tau + force;
     }
+    conserve_rounding(s, s_in, gx, gy);
 }
 
 }  // namespace mlbm
