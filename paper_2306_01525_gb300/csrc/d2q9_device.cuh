@@ -127,6 +127,9 @@ __device__ __forceinline__ void conserve_rounding(float (&s)[9], const float (&s
     }
 }
 
+// kConserve = false leaves out the re-rounding (the lattice LBM comparison path, whose per-node
+// arithmetic is small enough that it would cost throughput).
+template <bool kConserve = true>
 __device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, float inv_tau, float gx, float gy,
                                                   float &rho, float &ux, float &uy) {
     float s_in[9];
@@ -151,7 +154,7 @@ __device__ __forceinline__ void collide_projected(float (&s)[9], float rho_ref, 
         const float force = omega_of<float>(k) * 3.0f * (float(ex_of(k)) * gx + float(ey_of(k)) * gy);
         s[k] = s[k] - ne[k] * inv_tau + force;
     }
-    conserve_rounding(s, s_in, gx, gy);
+    if constexpr (kConserve) conserve_rounding(s, s_in, gx, gy);
 }
 
 }  // namespace mlbm

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) lattice_step_kernel(int64_t nx, int64_t n
         f[8] = __ldg(fin + 8 * N + rowp + xm);
         T rho, ux, uy;
         if constexpr (std::is_same<T, float>::value)
-            collide_projected(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
+            collide_projected<false>(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
         else
             collide<T>(f, rho_ref, inv_tau, gx, gy, rho, ux, uy);
 #pragma unroll
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) lattice_step4_kernel(int nx, int ny, Latt
         for (int r = 0; r < 4; ++r) {
             float f[9] = {f0[r], f1[r], f2[r], f3[r], f4[r], f5[r], f6[r], f7[r], f8[r]};
             float rho, ux, uy;
-            collide_projected(f, prm.rho032, prm.inv_tau32, prm.g32, 0.0f, rho, ux, uy);
+            collide_projected<false>(f, prm.rho032, prm.inv_tau32, prm.g32, 0.0f, rho, ux, uy);
 #pragma unroll
             for (int k = 0; k < 9; ++k) o[k][r] = f[k];
             m[0][r] = rho;
