@@ -544,6 +544,12 @@ def bench_adjoint(steps: int = 2000):
     bpn = adjoint_bytes_per_node(K)
     peak, _ = _peaks()
     gbs = bpn * n / (rev_us * 1e-6) / 1e9
+    # what a plain read of the same number of bytes takes, timed the same way (torch's sum over a
+    # contiguous buffer): at a few hundred MB a launch's ramp-up and tail are a visible part of
+    # its time, so this is the floor a kernel of this size can reach, below the copy peak
+    plain = torch.ones(bpn * n // 4, dtype=torch.float32, device=dev)
+    read_us = kernel_us(lambda: torch.sum(plain, dim=0, out=sink))
+    del plain
     return {"workload": "annulus_250k_k24_d3_adjoint", "nodes": n, "steps": steps, "dtype": "f32",
             "checkpoint_every": int(np.ceil(np.sqrt(steps))), "forward_s": t_fwd,
             "forward_backward_s": t_all, "loss": float(loss.detach()),
@@ -553,6 +559,8 @@ def bench_adjoint(steps: int = 2000):
             "reverse_step": {"us": rev_us, "us_recompute_route": rev_rc_us, "forward_step_us": fwd_us,
                              "algorithmic_bytes_per_node": bpn, "achieved_gbs": gbs,
                              "frac_of_hbm": gbs / peak,
+                             "plain_read_same_bytes": {"us": read_us, "gbs": bpn * n / (read_us * 1e-6) / 1e9,
+                                                       "reverse_step_frac": read_us / rev_us},
                              "nearest_rule": {"us": rev_near_us, "forward_step_us": fwd_near_us},
                              "l2": "flushed before each launch (256 MB write, then 256 MB read)"}}
 
