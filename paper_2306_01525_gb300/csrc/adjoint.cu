@@ -376,8 +376,12 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
         const int U = a.rcnt[t];
         const int32_t *__restrict__ rh = a.rhalo + a.roff[t];
         T dtau = T(0), dg = T(0);
+        // the next iteration's halo index is loaded one iteration ahead (its latency overlaps the
+        // current node's loads)
+        int32_t node_next = b < U ? rh[b] : 0;
         for (int u = b; u < U; u += B) {
-            const int64_t node = rh[u];
+            const int64_t node = node_next;
+            if (u + B < U) node_next = rh[u + B];
             T mt[8];
             if constexpr (kFromNext) {
                 local_from_next<T>(a, node, tile.seg, u < tile.count, mt, dtau, dg);
@@ -500,6 +504,9 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
                 const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
                 for (int sg = 0; sg < a.nseg; ++sg) {
                     double s0 = 0.0, s1 = 0.0;
+                    // the running gradient is read before the tile sums (its latency overlaps theirs)
+                    double2 g_old = make_double2(0.0, 0.0);
+                    if (threadIdx.x == 0) g_old = make_double2(__ldcg(a.grad + 2 * sg), __ldcg(a.grad + 2 * sg + 1));
                     // eight tiles' segments and sums loaded before any is added (one memory
                     // latency per eight tiles, not two per tile)
                     for (int t0 = threadIdx.x; t0 < a.ntiles; t0 += 8 * B) {
@@ -535,8 +542,8 @@ __global__ void __launch_bounds__(B) adj_pull_kernel(AdjArgs<T> a) {
                             g0 += red[0][q];
                             g1 += red[1][q];
                         }
-                        a.grad[2 * sg] += g0;
-                        a.grad[2 * sg + 1] += g1;
+                        a.grad[2 * sg] = g_old.x + g0;
+                        a.grad[2 * sg + 1] = g_old.y + g1;
                     }
                     __syncthreads();
                 }
