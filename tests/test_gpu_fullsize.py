@@ -72,6 +72,54 @@ def test_full_size_one_step_sampled_parity(big):
             assert abs(m[2] - v_o) < atol, (i, dtype, m[2], v_o)
 
 
+def test_full_size_three_single_steps_sampled_parity(big):
+    """Per-step parity at full size over three consecutive steps, in both precisions: each GPU
+    step, from the GPU's own state of the previous level, matches at sampled nodes the oracle's
+    streaming of that state (its own stencils and shape vectors, checked equal to the GPU's
+    stencils) followed by its moments."""
+    xy, dx, cloud, w = big
+    n = w.n
+    rho, u, v = mi.tgv_initial(xy, U0)
+    perm = cloud.perm()
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(n)
+    t = lambda a: torch.as_tensor(a, dtype=torch.float64, device="cuda:0")
+    params = [(TAU, 0.0, 1.0)]
+    rng = np.random.default_rng(29)
+    sample = rng.choice(n, 16, replace=False)
+    st_gpu = cloud.stencil(0)
+    node_w = {}
+    for i in sample:
+        node_w[i] = oracle.node_weights(xy, int(i), K, DEG, dx, box=(1.0, 1.0))
+        np.testing.assert_array_equal(st_gpu[:, i], node_w[i][0][1])
+    omega = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    for dtype, td, atol in ((mlbm.F64, torch.float64, 1e-9), (mlbm.F32, torch.float32, 1e-8)):
+        a = torch.empty(9 * n, dtype=td, device="cuda:0")
+        b = torch.empty_like(a)
+        mom = torch.empty(3 * n, dtype=td, device="cuda:0")
+        mlbm.init(w, params, dtype, t(rho), t(u), t(v), a)
+        for step in range(3):
+            mlbm.step(w, params, dtype, a, b, mom)
+            # the previous level's post-collision populations, original node order (the FP32
+            # state holds deviations from omega_k rho0)
+            prev = a.view(9, n).cpu().numpy().astype(np.float64)
+            if dtype == mlbm.F32:
+                prev += omega[:, None]
+            post = np.empty_like(prev)
+            post[:, perm] = prev
+            got = mom.view(3, n).cpu().numpy().astype(np.float64)
+            for i in sample:
+                sidx, W = node_w[i]
+                f = np.array([W[k] @ post[k, sidx[k]] for k in range(9)])
+                r_o, u_o, v_o = oracle.moments(f)
+                m = got[:, inv[i]]
+                assert abs(m[0] - r_o) < 10 * atol, (step, i, dtype, m[0], r_o)
+                assert abs(m[1] - u_o) < atol, (step, i, dtype, m[1], u_o)
+                assert abs(m[2] - v_o) < atol, (step, i, dtype, m[2], v_o)
+            a, b = b, a
+        del a, b, mom
+
+
 def test_full_size_fp32_tracks_fp64(big):
     """Whole-field check at full size: after 200 steps the FP32 deviation-storage path stays
     within 1e-6 relative L2 of the FP64 path (same shape vectors)."""
