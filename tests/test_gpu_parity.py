@@ -404,6 +404,42 @@ def test_annulus_step_with_force_and_bounce_back_matches_oracle(dtype):
     np.testing.assert_allclose(v_g.cpu().numpy(), v_o, atol=tol * 1e-1)
 
 
+def test_annulus_20k_workload_per_step_parity():
+    """The annular-channel workload at its own size and in the launch configuration the
+    benchmark times (about 20k scattered nodes refined toward the walls, seed 2, N_L = 20, P_3,
+    dx_ml = 1/320, tau = 0.7, g = 1e-6, FP64, one-warp tiles): ten steps from a perturbed rest
+    state, each stored state equal to the oracle's post-collision populations to 1e-12 (oracle
+    shape vectors uploaded, Q20), with the azimuthal force and wall bounce-back."""
+    dx, K, deg, tau, g = 1.0 / 320, 20, 3, 0.7, 1e-6
+    xy, wall = mi.annulus_cloud(h=mi.ANNULUS_H_FOR[20000], seed=2)
+    seg = dict(geometry=mlbm.ANNULUS, r_in=0.5, r_out=1.0, k=K, degree=deg, dx_ml=dx)
+    cloud = mlbm.build_cloud(xy, seg)
+    w = mlbm.build_weights(cloud)
+    sidx, W = oracle.weights(xy, K, deg, dx)
+    w.upload(W[1:], sidx[1].astype(np.int32))
+    mask = oracle.bounce_mask(xy, dx, 0.5, 1.0)
+    assert np.array_equal(cloud.bounce_mask(), mask) and mask.any()
+    force = oracle.azimuthal_force(xy, g)
+    st = oracle.Stepper(sidx, W, tau, mask=mask, force=force)
+    n = xy.shape[1]
+    rng = np.random.default_rng(4)
+    rho = 1.0 + 1e-4 * rng.standard_normal(n)
+    u = 1e-4 * rng.standard_normal(n)
+    v = 1e-4 * rng.standard_normal(n)
+    params = [(tau, g, 1.0)]
+    fa = _gpu_init(w, params, mlbm.F64, rho, u, v)
+    fb = torch.empty_like(fa)
+    f_or = oracle.init_equilibrium(rho, u, v)
+    perm = cloud.perm()
+    for it in range(10):
+        mlbm.step(w, params, mlbm.F64, fa, fb)
+        fa, fb = fb, fa
+        f_or = st.step(f_or)
+        post = oracle.collide_field(f_or, tau, force)
+        got = _to_orig(fa.view(9, n).cpu().numpy(), perm)
+        assert np.max(np.abs(got - post)) <= STEP_TOL * np.max(np.abs(post)), it
+
+
 # ----------------------------------------------------------------------------- batching
 
 def test_batched_segments_match_single_runs_and_oracle():
